@@ -1,0 +1,176 @@
+"""Pins of the oracle's time stepping against conservation laws, closed forms
+and a boundary-value solution of the paper's porous-channel equation (CPU only)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1406_6438_gb300 import workloads as W
+from tests._closed_forms import brinkman, porous_bvp, poiseuille_series
+
+CS2 = 1.0 / 3.0
+
+
+@pytest.mark.parametrize("q,shape,wm", [(9, (1, 24, 20), 0), (9, (1, 24, 20), 2),
+                                        (19, (10, 12, 8), 6), (19, (6, 6, 6), 0)])
+def test_mass_conservation(q, shape, wm):
+    """Sum over cells and directions of f is invariant: collision conserves it
+    (sum f^eq = eps rho, sum P_i = sum F_i = 0) and so do periodic wrap and
+    half-way bounce-back.  Non-uniform eps, drag and body force all on."""
+    nz, ny, nx = shape
+    p = O.Params(q=q, nx=nx, ny=ny, nz=nz, wall_mask=wm, tau=0.62, g=(3e-5, 1e-5, -2e-5),
+                 drag_mode=2, k_mode=0, d_p=8.0)
+    eps = W.smoothed_noise(shape, 3.0, 0.4, 1.0, seed=7).astype(np.float64)
+    f = O.init(p, eps)
+    m0 = f.sum()
+    f = O.run(p, eps, f, 200)
+    assert abs(f.sum() - m0) <= 1e-13 * m0
+
+
+def test_momentum_conservation_uniform_eps():
+    """Uniform eps, no drag, no body force, periodic: grad eps = 0 and F = 0, so
+    the sources vanish and collision conserves momentum exactly."""
+    q, shape = 9, (1, 16, 18)
+    p = O.Params(q=q, nx=18, ny=16, wall_mask=0, tau=0.7)
+    eps = np.full(shape, 0.7)
+    f = W.random_state(q, eps.astype(np.float32), seed=3, amp=0.05).astype(np.float64)
+    e, _, _ = O.lattice(q)
+    j0 = np.einsum("ia,izyx->a", e[:, :2].astype(float), f)
+    f = O.run(p, eps, f, 100)
+    j1 = np.einsum("ia,izyx->a", e[:, :2].astype(float), f)
+    assert np.abs(j1 - j0).max() < 1e-14
+
+
+@pytest.mark.parametrize("q", [9, 19])
+def test_poiseuille_exact_at_magic_tau(q):
+    """eps = 1 and no drag reduce the model to LBGK with Guo forcing.  With
+    half-way bounce-back, plane Poiseuille flow is then parabolic exactly at the
+    nodes when (tau - 1/2)^2 = 3/16 (a known special case of the BGK wall slip):
+    u(y) = g/(2 nu) y (H - y) at y = j + 1/2."""
+    H = 8
+    tau = 0.5 + np.sqrt(3.0 / 16.0)
+    nu = CS2 * (tau - 0.5)
+    g = 1e-6
+    if q == 9:
+        p = O.Params(q=9, nx=3, ny=H, wall_mask=2, tau=tau, g=(g, 0, 0))
+    else:
+        p = O.Params(q=19, nx=3, ny=H, nz=2, wall_mask=2, tau=tau, g=(g, 0, 0))
+    eps = np.ones(p.shape)
+    f = O.run(p, eps, O.init(p, eps), 4000)
+    _, u = O.moments(p, eps, f)
+    y = np.arange(H) + 0.5
+    ex = g / (2 * nu) * y * (H - y)
+    prof = u[0, 0, :, 0]
+    assert np.abs(prof - ex).max() <= 1e-10 * ex.max()
+    assert np.abs(u[1]).max() <= 1e-14
+
+
+def test_poiseuille_startup_series():
+    """eps = 1: start-up Poiseuille against the exact continuum series, within the
+    O(H^-2) discretisation error (about 1e-3 at H = 32, tau = 0.8)."""
+    H, tau, g = 32, 0.8, 1e-6
+    nu = CS2 * (tau - 0.5)
+    p = O.Params(q=9, nx=1, ny=H, wall_mask=2, tau=tau, g=(g, 0, 0))
+    eps = np.ones(p.shape)
+    f = O.init(p, eps)
+    y = np.arange(H) + 0.5
+    for T in (500, 2000):
+        fT = O.run(p, eps, f, T)
+        _, u = O.moments(p, eps, fT)
+        ex = poiseuille_series(y, T, g, nu, H)
+        assert np.abs(u[0, 0, :, 0] - ex).max() <= 3e-3 * ex.max()
+
+
+def test_brinkman_second_order():
+    """Uniform eps, Darcy drag only: the steady profile converges to the Brinkman
+    closed form of nu u'' - (eps nu / K) u + g = 0 at second order in 1/H."""
+    tau, e, Da, g = 0.8, 0.6, 1e-2, 1e-6
+    nu = CS2 * (tau - 0.5)
+    errs = []
+    for H in (16, 32, 64):
+        K = Da * H * H
+        p = O.Params(q=9, nx=1, ny=H, wall_mask=2, tau=tau, g=(g, 0, 0), drag_mode=1,
+                     k_mode=1, K=K)
+        eps = np.full(p.shape, e)
+        f = O.run(p, eps, O.init(p, eps), int(20 * H * H / (100 * nu)) + 3000)
+        _, u = O.moments(p, eps, f)
+        y = np.arange(H) + 0.5
+        ex = brinkman(y, g, nu, e, K, H)
+        errs.append(np.abs(u[0, 0, :, 0] - ex).max() / ex.max())
+    assert errs[-1] < 1.5e-3
+    ratios = np.array(errs[:-1]) / np.array(errs[1:])
+    assert np.all(ratios > 3.0), ratios
+
+
+def test_forchheimer_channel_against_bvp():
+    """The 128x64 channel workload (uniform eps = 0.6, Da = 1e-3, Forchheimer on)
+    at steady state against a 4001-point Newton solution of the paper's porous
+    channel equation with a body force, nu u'' - (eps nu/K) u - (eps^2 F_eps/sqrt K)
+    |u| u + g = 0 (the printed d/dx is read as d/dy).  The discretisation error at
+    H = 64 is below 1 %, and halves at least 2.5x from H = 32 to 64."""
+    params, eps32, _ = W.channel_128x64()
+    tau = params["tau"]
+    nu = CS2 * (tau - 0.5)
+    e = float(eps32.flat[0])
+    errs = []
+    for H in (32, 64):
+        K = 1e-3 * H * H
+        Feps = 1.75 / np.sqrt(150 * e ** 3)
+        U = nu / H
+        g = U * e * nu / K + e ** 2 * Feps / np.sqrt(K) * U * U
+        p = O.Params(q=9, nx=1, ny=H, wall_mask=2, tau=tau, g=(g, 0, 0), drag_mode=2,
+                     k_mode=2, K=K)
+        eps = np.full(p.shape, e)
+        f = O.run(p, eps, O.init(p, eps), 6000)
+        _, u = O.moments(p, eps, f)
+        yb, ub = porous_bvp(nu, e, K, Feps, g, H)
+        y = np.arange(H) + 0.5
+        ref = np.interp(y, yb, ub)
+        errs.append(np.abs(u[0, 0, :, 0] - ref).max() / ref.max())
+    assert errs[1] < 1e-2
+    assert errs[0] / errs[1] > 2.5
+    # the workload's own force gives Re = U H / nu close to 1
+    p = O.Params(**{k: v for k, v in params.items()})
+    p.nx = 1
+    eps = np.full(p.shape, e)
+    f = O.run(p, eps, O.init(p, eps), 5000)
+    _, u = O.moments(p, eps, f)
+    Re = u[0].max() * 64 / nu
+    assert 0.95 < Re < 1.05
+
+
+def test_uniform_eps_scaling_invariance():
+    """With eps uniform the scheme is linear-homogeneous in f: the run with eps,
+    drag (alpha, beta) and force per mass g equals eps times the eps = 1 run with
+    drag (alpha/eps, beta/eps) -- i.e. K -> K/eps and F_eps -> eps^1.5 F_eps for
+    fixed K, F_eps.  Exact up to rounding (derived from Eqs. d2q9eq, Fi and 1moment)."""
+    e, K, Feps, tau = 0.45, 3.0, 0.4, 0.7
+    shape = (1, 12, 10)
+    base = dict(q=9, nx=10, ny=12, wall_mask=2, tau=tau, g=(4e-5, 1e-5, 0), drag_mode=2, k_mode=1)
+    p_e = O.Params(**base, K=K, F_eps=Feps)
+    p_1 = O.Params(**base, K=K / e, F_eps=Feps * e ** 1.5)
+    eps_e = np.full(shape, e)
+    eps_1 = np.ones(shape)
+    f_e = O.run(p_e, eps_e, O.init(p_e, eps_e), 300)
+    f_1 = O.run(p_1, eps_1, O.init(p_1, eps_1), 300)
+    assert np.abs(f_e - e * f_1).max() <= 1e-14
+    _, u_e = O.moments(p_e, eps_e, f_e)
+    _, u_1 = O.moments(p_1, eps_1, f_1)
+    assert np.abs(u_e - u_1).max() <= 1e-12 * np.abs(u_1).max()
+
+
+def test_quiescent_porous_box_stays_near_rest():
+    """No force, periodic box, non-uniform eps: the volume-averaged equations are
+    at rest with uniform pressure.  The discrete P_i term and the eps-weighted
+    equilibrium do not cancel exactly on the lattice, so a small spurious flow
+    appears and settles; it stays bounded (recorded: max|u| about 4.3e-3 and
+    rho within 2 % of 1 for a field in [0.4, 1.0] smoothed over sigma = 4 cells)
+    and mass is conserved to rounding."""
+    shape = (1, 32, 32)
+    p = O.Params(q=9, nx=32, ny=32, wall_mask=0, tau=0.8)
+    eps = W.smoothed_noise(shape, 4.0, 0.4, 1.0, seed=9).astype(np.float64)
+    f0 = O.init(p, eps)
+    f = O.run(p, eps, f0, 1000)
+    _, u = O.moments(p, eps, f)
+    umax = np.abs(u).max()
+    assert np.isfinite(umax) and umax < 1e-2
+    assert abs(f.sum() - f0.sum()) <= 1e-12 * f0.sum()
