@@ -1,0 +1,408 @@
+"""Benchmark of the porous (VANS) lattice Boltzmann step on GB300.
+
+Default workload: D2Q9, 4096 x 4096 periodic domain, eps from seeded
+Gaussian-smoothed noise (sigma = 16 cells) in [0.4, 1.0], tau = 0.6, Ergun
+drag, body force along x, FP32 populations.  One "step" is one fused
+collide-and-stream update of the whole domain (all 16.8 M cells).
+
+Prints one JSON line: MLUPS (device time, CUDA events on the launching
+stream), the HBM roofline of the step kernel, an end-to-end figure through the
+public API with host buffers, SM clocks sampled during the timed region, the
+FP64 CPU oracle timed on a bounded sample, and beside the plain step the MLUPS
+of the D3Q19 duct, the batched 256-domain run and the adjoint (reverse) pass.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank runs the same workload on its own GPU (the
+domains are independent replicas: no collective on the data path); value is
+the sum over ranks, timed by the slowest rank.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and % of HBM-bandwidth roofline; batched and adjoint MLUPS vs plain"
+WORKLOAD = ("D2Q9 4096x4096 periodic, eps smoothed noise (sigma 16) in [0.4,1.0], tau 0.6, "
+            "Ergun drag (d_p 21.33) + Forchheimer, body force along x, FP32 populations")
+BYTES_PER_CELL = {9: 9 * 4 * 2 + 4, 19: 19 * 4 * 2 + 4}     # algorithmic bytes per update
+FALLBACK_HBM_GBS = 6800.0
+
+# DRAM bytes per launch of the D2Q9 step kernel measured by ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by a hash of the kernel
+# sources they were taken on; a changed kernel reports null.
+TRAFFIC = {}
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("vans_step.cu", "vans_device.cuh"):
+        with open(os.path.join(ROOT, "paper_1406_6438_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev_id: str | None):
+        self.dev_id = dev_id
+        self.proc = None
+        self.err = None
+
+    def __enter__(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "100"]
+        if self.dev_id:
+            cmd += ["-i", self.dev_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+            time.sleep(0.25)
+        except Exception as e:   # no nvidia-smi: report it
+            self.err = str(e)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+        return False
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "error": self.err}
+        sm, smax, reasons, power = [], None, set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            c = [x.strip() for x in ln.split(",")]
+            if len(c) < 9:
+                continue
+            try:
+                sm.append(float(c[1]))
+                smax = float(c[2])
+                power.append(float(c[3]))
+            except ValueError:
+                continue
+            for name, v in zip(names, c[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def gpu_uuid(torch, dev):
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------- CPU oracle --
+def oracle_mlups(p: dict, eps: np.ndarray, budget_s: float, max_steps: int | None = None):
+    """Time the FP64 oracle on (p, eps): steps until about budget_s seconds."""
+    import oracle as O
+    po = O.Params(**p)
+    e = eps.astype(np.float64)
+    f = O.init(po, e)
+    t0 = time.perf_counter()
+    f = O.run(po, e, f, 1)
+    one = time.perf_counter() - t0
+    n = max(1, int(budget_s / max(one, 1e-6)))
+    if max_steps:
+        n = min(n, max_steps)
+    t0 = time.perf_counter()
+    O.run(po, e, f, n)
+    dt = time.perf_counter() - t0
+    cells = p["nx"] * p["ny"] * p["nz"]
+    return cells * n / dt / 1e6, n, dt, O.num_threads()
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                if ln.lower().startswith(("model name", "cpu part")):
+                    return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return os.uname().machine
+
+
+# -------------------------------------------------------- reference arm ----
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_1406_6438_gb300 import workloads as W
+    import oracle as O
+    O.build()
+    p, eps, _ = W.periodic_2d(4096)
+    # the step of this arm: one FP64 update of a 512 x 512 periodic crop of the
+    # workload's eps field (a bounded sample of the same workload)
+    crop = np.ascontiguousarray(eps[:, :512, :512])
+    pc = dict(p, nx=512, ny=512)
+    po = O.Params(**pc)
+    e = crop.astype(np.float64)
+    f = O.init(po, e)
+    f = O.run(po, e, f, max(args.warmup, 0))
+    t0 = time.perf_counter()
+    O.run(po, e, f, args.steps)
+    dt = time.perf_counter() - t0
+    cells = 512 * 512
+    v = cells * args.steps / dt / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nx": 4096, "ny": 4096,
+                   "sample": "512x512 periodic crop of the 4096x4096 eps field"},
+        "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": O.num_threads(), "kind": "oracle",
+                         "sample": f"FP64 oracle, {args.steps} steps of a 512x512 crop",
+                         "cpu": cpu_model()},
+        "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------- GPU arm ---
+def time_region(torch, stream, fn):
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    fn()
+    b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b) / 1e3
+
+
+def bench_d3q19(torch, V, W):
+    p, eps, n = W.duct_3d()
+    s = V.Solver(p)
+    s.set_eps(torch.from_numpy(eps).cuda().view(-1))
+    L = s.autotune()
+    s.step(10)
+    c0 = s.launch_count
+    t = time_region(torch, s.stream, lambda: s.step(n))
+    cells = p["nx"] * p["ny"] * p["nz"]
+    out = {"workload": "D3Q19 256^3, walls y/z, eps noise [0.35,0.95], tau 0.6, Forchheimer",
+           "steps": n, "value": cells * n / t / 1e6, "unit": "MLUPS",
+           "gb_s": BYTES_PER_CELL[19] * cells * n / t / 1e9,
+           "launch": vars(L), "launches": s.launch_count - c0}
+    s.close()
+    return out
+
+
+def bench_batched(torch, V, W):
+    doms = W.batched_channels()
+    b = V.Batch([p for p, _ in doms])
+    for d, (_, eps) in enumerate(doms):
+        b.set_eps(d, torch.from_numpy(eps).cuda().view(-1))
+    L = b.autotune()
+    n = 2000
+    b.step(20)
+    c0 = b.launch_count
+    t = time_region(torch, b.stream, lambda: b.step(n))
+    cells = b.cells
+    out = {"workload": "256 D2Q9 channels, nx~U[64,1024], ny~U[32,512], own eps and tau",
+           "domains": len(doms), "cells": cells, "steps": n,
+           "value": cells * n / t / 1e6, "unit": "MLUPS",
+           "gb_s": BYTES_PER_CELL[9] * cells * n / t / 1e9,
+           "launch": vars(L), "launches": b.launch_count - c0}
+    b.close()
+    return out
+
+
+def bench_adjoint(torch, V, W):
+    from paper_1406_6438_gb300.adjoint import outlet_flux
+    p, eps, n, every = W.adjoint_channel()
+    s = V.Solver(p)
+    s.set_eps(torch.from_numpy(eps).cuda().view(-1))
+    s.autotune()
+    e = torch.from_numpy(eps).cuda().requires_grad_(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J = outlet_flux(e, s, n, every)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    c0 = s.launch_count
+    J.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    cells = p["nx"] * p["ny"]
+    out = {"workload": "D2Q9 512x512 channel, eps noise [0.4,1.0], tau 0.8, outlet flux gradient",
+           "steps": n, "checkpoint_every": every,
+           "value": cells * n / (t2 - t1) / 1e6, "unit": "MLUPS (backward pass, wall clock)",
+           "forward_mlups": cells * n / (t1 - t0) / 1e6,
+           "backward_launches": s.launch_count - c0,
+           "grad_finite": bool(torch.isfinite(e.grad).all().item())}
+    s.close()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--n", type=int, default=4096, help="domain edge (default 4096)")
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    import paper_1406_6438_gb300 as V
+    from paper_1406_6438_gb300 import workloads as W
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    p, eps, _ = W.periodic_2d(args.n)
+    cells = p["nx"] * p["ny"]
+    sim = V.Solver(p)
+    sim.set_eps(torch.from_numpy(eps).cuda().view(-1))
+    L = sim.autotune()
+    sim.step(args.warmup)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    c0 = sim.launch_count
+    with ClockSampler(gpu_uuid(torch, local)) as clk:
+        t = time_region(torch, sim.stream, lambda: sim.step(args.steps))
+    launches = sim.launch_count - c0
+    if dist:
+        tt = torch.tensor([t], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = tt.item()
+    ok = sim.check()
+    value = world * cells * args.steps / t / 1e6
+    per_launch = t / args.steps
+    peak, peak_kind = peaks()
+    achieved = BYTES_PER_CELL[9] * cells / per_launch / 1e9
+    traffic = TRAFFIC.get(kernel_hash()) if args.n == 4096 else None
+
+    # end to end through the public API with host buffers: upload eps from
+    # pinned host memory, set_eps, K steps, moments, copy rho and u back
+    eps_host = torch.from_numpy(eps).view(-1).pin_memory()
+    rho_host = torch.empty(cells, dtype=torch.float32).pin_memory()
+    u_host = torch.empty(2 * cells, dtype=torch.float32).pin_memory()
+    eps_dev = torch.empty(cells, dtype=torch.float32, device="cuda")
+    rho_dev = torch.empty(cells, dtype=torch.float32, device="cuda")
+    u_dev = torch.empty(2 * cells, dtype=torch.float32, device="cuda")
+
+    def e2e():
+        eps_dev.copy_(eps_host, non_blocking=True)
+        sim.set_eps(eps_dev)
+        sim.step(args.steps)
+        sim.moments(rho_dev, u_dev)
+        rho_host.copy_(rho_dev, non_blocking=True)
+        u_host.copy_(u_dev, non_blocking=True)
+
+    with torch.cuda.stream(sim.stream):
+        t_e2e = time_region(torch, sim.stream, e2e)
+    if dist:
+        tt = torch.tensor([t_e2e], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_e2e = tt.item()
+    h2d = cells * 4
+    d2h = 3 * cells * 4
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+
+    extras = {}
+    cpu = None
+    if world == 1 and not args.no_extras:
+        for name, fn in (("d3q19", bench_d3q19), ("batched", bench_batched),
+                         ("adjoint", bench_adjoint)):
+            try:
+                extras[name] = fn(torch, V, W)
+            except Exception as ex:       # report, keep the headline line
+                extras[name] = {"error": repr(ex)}
+            torch.cuda.empty_cache()
+    if world == 1 and rank == 0 and not args.no_cpu:
+        import oracle as O
+        O.build()
+        mlups, n_or, dt, cores = oracle_mlups(p, eps, budget_s=12.0)
+        cpu = {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+               "sample": f"FP64 oracle, {n_or} steps of the full {args.n}x{args.n} workload "
+                         f"({dt:.1f} s)", "cpu": cpu_model()}
+
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nx": args.n, "ny": args.n, "cells": cells,
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (two 0.6 GB population buffers), no flush",
+                   "launch": vars(L)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_kind": peak_kind, "bytes_per_cell": BYTES_PER_CELL[9],
+                     "kernel": "k_step<9,cpt>", "launch_us": per_launch * 1e6},
+        "e2e": {"value": world * cells * args.steps / t_e2e / 1e6, "unit": "MLUPS",
+                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+                "note": "per K-step job: eps H2D, set_eps, K steps, moments, rho+u D2H"},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "state_ok": ok,
+        "cpu_baseline": cpu,
+    }
+    line.update(extras)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,210 @@
+/*
+ * vans.h -- C ABI of the GB300 (sm_103a) porous lattice Boltzmann library.
+ *
+ * The library advances the lattice Boltzmann model for the volume-averaged
+ * Navier-Stokes equations of Zhang, Wang & Ouyang ("Lattice Boltzmann Model for
+ * the Volume-Averaged Navier-Stokes Equations"):
+ *
+ *   f_i(x + e_i, t + 1) - f_i(x, t) = -(f_i - f_i^eq)/tau + P_i + F_i
+ *
+ * with the porosity-weighted equilibrium (Eq. d2q9eq), the pressure correction
+ * P_i (Eq. pi), the Guo forcing term F_i (Eq. Fi) carrying the body force and the
+ * Darcy/Forchheimer drag (drag law and the Ergun K, F_eps of the "Examples and
+ * discussions" section), and the moments eps*rho, eps*rho*u of Eqs. 0moment and
+ * 1moment.  Walls are half-way bounce-back; x is always periodic.
+ *
+ * Conventions for every entry point:
+ *   - All array pointers are DEVICE pointers (CUDA global memory) unless stated.
+ *     The caller allocates and owns every buffer, including the workspace; the
+ *     library owns only the handle (host memory) and never frees caller memory.
+ *   - Work is enqueued asynchronously on the stream given to vans_create; a call
+ *     returns before the GPU has finished.  Launch errors are reported; errors
+ *     that happen later on the device surface at the next call or sync.
+ *   - Every int-returning call returns VANS_OK (0) or a negative VANS_ERR_*.
+ *     No exception crosses the ABI.  A NULL handle gives VANS_ERR_ARG.
+ *   - Dense field layout ("dense"): x fastest, then y, then z; a vector field
+ *     stores its components one after the other (component-major).  For D2Q9,
+ *     nz = 1 and vectors have 2 components; for D3Q19 they have 3.
+ *   - Direction order.  D2Q9: 0 (0,0), 1 (1,0), 2 (0,1), 3 (-1,0), 4 (0,-1),
+ *     5 (1,1), 6 (-1,1), 7 (-1,-1), 8 (1,-1).  D3Q19: 0 (0,0,0), 1 (1,0,0),
+ *     2 (-1,0,0), 3 (0,1,0), 4 (0,-1,0), 5 (0,0,1), 6 (0,0,-1), 7 (1,1,0),
+ *     8 (-1,-1,0), 9 (1,-1,0), 10 (-1,1,0), 11 (1,0,1), 12 (-1,0,-1),
+ *     13 (1,0,-1), 14 (-1,0,1), 15 (0,1,1), 16 (0,-1,-1), 17 (0,1,-1), 18 (0,-1,1).
+ *   - "state" buffers hold the populations in the library's own padded layout
+ *     (vans_state_floats() floats each, 16-byte aligned).  Their content is the
+ *     post-collision populations of the previous step stored as deviations from
+ *     w_i * eps; use vans_get_populations() for the physical f_i(x, t).
+ */
+#ifndef VANS_H
+#define VANS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    VANS_OK = 0,
+    VANS_ERR_ARG = -1,          /* bad argument, size, pointer or parameter          */
+    VANS_ERR_CUDA = -2,         /* a CUDA call or kernel launch failed                */
+    VANS_ERR_DIVERGED = -3,     /* non-finite or supersonic state detected            */
+    VANS_ERR_TIMEOUT = -4,      /* a bounded device wait gave up                      */
+    VANS_ERR_UNSUPPORTED = -5,  /* valid request this build does not implement        */
+    VANS_ERR_STATE = -6         /* call out of order (e.g. step before set_eps)       */
+};
+
+typedef struct vans_s *vans_t; /* opaque handle, owned by the library */
+
+/* Model and domain parameters of one domain. */
+typedef struct {
+    int q;          /* 9 (D2Q9) or 19 (D3Q19)                                        */
+    int nx, ny, nz; /* lattice size; nz must be 1 for D2Q9; each >= 1                */
+    int wall_mask;  /* bit1: bounce-back walls on both y faces; bit2: on both z faces;
+                       a cleared bit means periodic.  bit0 (x walls) is unsupported. */
+    float tau;      /* relaxation time, > 0.5; nu = (tau - 1/2)/3 (after Eq. VNS2)   */
+    float g[3];     /* body force per unit mass; the force density is eps*rho*g      */
+    int drag_mode;  /* 0 none, 1 Darcy only, 2 Darcy + Forchheimer (drag law)        */
+    int k_mode;     /* 0: Ergun K(eps) = eps^3 d_p^2 / (150 (1-eps)^2) and
+                          F_eps(eps) = 1.75 / sqrt(150 eps^3);
+                       1: K and F_eps fixed (fields K, F_eps);
+                       2: K fixed, F_eps(eps) = 1.75 / sqrt(150 eps^3)                 */
+    float d_p;      /* particle diameter (k_mode 0)                                  */
+    float K;        /* permeability (k_mode 1, 2)                                    */
+    float F_eps;    /* geometric function (k_mode 1)                                 */
+} vans_params;
+
+/* Launch configuration of the step kernels (chosen by vans_autotune). */
+typedef struct {
+    int cpt;        /* cells per thread along x: 1, 2 or 4                           */
+    int warps;      /* warps per block along x: 1..8                                 */
+    int rows;       /* rows (y, or y*z lines) per block: 1..8                        */
+} vans_launch;
+
+/* ---------------------------------------------------------------- sizes -- */
+
+/* Floats in one state buffer for these parameters, or -1 if they are invalid. */
+long long vans_state_floats(const vans_params *p);
+
+/* Bytes of workspace vans_create needs (two state buffers, a padded copy of eps
+ * and a few status words), or 0 if the parameters are invalid. */
+size_t vans_workspace_bytes(const vans_params *p);
+
+/* ------------------------------------------------------------ lifecycle -- */
+
+/* Validate p and build a handle that uses `workspace` (device memory of at
+ * least vans_workspace_bytes(p) bytes, 256-byte aligned; owned by the caller and
+ * it must outlive the handle) and enqueues on `cuda_stream` (a cudaStream_t;
+ * NULL is the legacy default stream).  Allocates no device memory.
+ * Errors: VANS_ERR_ARG (invalid p, small or misaligned workspace, NULL out),
+ * VANS_ERR_UNSUPPORTED (x walls). */
+int vans_create(const vans_params *p, void *workspace, size_t workspace_bytes,
+                void *cuda_stream, vans_t *out);
+
+/* Release the handle and its CUDA graphs.  Never frees caller memory. */
+void vans_destroy(vans_t h);
+
+/* Copy the porosity field eps (dense, nx*ny*nz floats, device) into the
+ * workspace and reset the populations to rest, rho = 1 and u = 0, i.e.
+ * f_i = w_i eps (the initial state of the validation case).  Every eps must
+ * satisfy 0 < eps <= 1; otherwise VANS_ERR_ARG and the handle keeps its
+ * previous state.  (Synchronises the stream once to check the range.) */
+int vans_set_eps(vans_t h, const float *eps_dev);
+
+/* ----------------------------------------------------------- time step -- */
+
+/* Advance the current state by nsteps >= 0 steps of the final LBE with P_i and
+ * F_i.  Long runs replay a captured CUDA graph.  Errors: VANS_ERR_STATE before
+ * vans_set_eps, VANS_ERR_ARG for nsteps < 0, VANS_ERR_CUDA. */
+int vans_step(vans_t h, int nsteps);
+
+/* One step from the caller's state buffer `in` to the caller's state buffer
+ * `out` (both vans_state_floats() floats; they must not overlap).  Uses the
+ * handle's eps and parameters; the handle's own state is untouched. */
+int vans_step_raw(vans_t h, const float *in, float *out);
+
+/* rho (dense, N floats) and u (dense, D*N floats) of the current state: the
+ * moments of Eqs. 0moment and 1moment, with the drag solved in closed form.
+ * Either pointer may be NULL to skip it. */
+int vans_moments(vans_t h, float *rho_dev, float *u_dev);
+
+/* Physical populations f_i(x, t) of the current state, dense [q][nz][ny][nx]. */
+int vans_get_populations(vans_t h, float *f_dev);
+
+/* Replace the current state by the physical populations f (dense [q][nz][ny][nx]). */
+int vans_set_populations(vans_t h, const float *f_dev);
+
+/* Raw copies of the current state (checkpoints; vans_state_floats() floats). */
+int vans_get_state(vans_t h, float *state_dev);
+int vans_set_state(vans_t h, const float *state_dev);
+
+/* Pick the fastest launch configuration for this domain by timing candidates
+ * on the handle's own buffers (the state is not changed).  Synchronises.
+ * `chosen` may be NULL. */
+int vans_autotune(vans_t h, vans_launch *chosen);
+
+/* Read or force the launch configuration (invalid values give VANS_ERR_ARG). */
+int vans_get_launch(vans_t h, vans_launch *cfg);
+int vans_set_launch(vans_t h, const vans_launch *cfg);
+
+/* -------------------------------------------------------------- adjoint -- */
+/* Reverse mode for J = sum over the plane x = x_out of eps*rho*u_x (Eq. 1moment)
+ * at the final step.  A "lambda" buffer has the state layout and holds dJ/df*
+ * of the populations a state buffer stores.  grad_acc is dense, (1 + D) * N
+ * floats: dJ/deps(x) collected so far, then dJ/d(grad eps)(x) per component. */
+
+/* J of a state buffer (NULL = the current state) written to J_dev[0] (FP32,
+ * fixed-order reduction).  Errors: VANS_ERR_ARG for x_out outside [0, nx). */
+int vans_flux(vans_t h, const float *state, int x_out, float *J_dev);
+
+/* Start the reverse pass: lam (lambda of `state`, NULL = current state) is set
+ * to dJ/df*; grad_acc is overwritten with the direct partials of J. */
+int vans_flux_seed(vans_t h, const float *state, int x_out, float *lam_dev, float *grad_acc);
+
+/* One reverse step through the forward step that read `state_t`: lam_out =
+ * (d step / d state)^T lam_in, and the eps partials of that step are added
+ * into grad_acc.  state_t, lam_in and lam_out must be distinct buffers. */
+int vans_step_adjoint(vans_t h, const float *state_t, const float *lam_in, float *lam_out,
+                      float *grad_acc);
+
+/* dJ/deps (dense, N floats) from the lambda of the initial state and grad_acc:
+ * adds the initial condition f = w eps and the transposed grad-eps stencil. */
+int vans_grad_finalize(vans_t h, const float *lam0, const float *grad_acc, float *dJdeps_dev);
+
+/* -------------------------------------------------------------- batched -- */
+/* n independent D2Q9 domains (each its own size, eps, tau and parameters)
+ * advanced by one persistent kernel per step over a flattened tile list.  The
+ * domain index d selects a domain in the calls that take it. */
+
+size_t vans_batch_workspace_bytes(const vans_params *p, int n);
+int vans_batch_create(const vans_params *p, int n, void *workspace, size_t workspace_bytes,
+                      void *cuda_stream, vans_t *out);
+/* eps of domain d (dense ny*nx floats); resets that domain to rest. */
+int vans_batch_set_eps(vans_t h, int d, const float *eps_dev);
+int vans_batch_step(vans_t h, int nsteps);
+int vans_batch_moments(vans_t h, int d, float *rho_dev, float *u_dev);
+int vans_batch_get_populations(vans_t h, int d, float *f_dev);
+int vans_batch_autotune(vans_t h, vans_launch *chosen);
+/* Cells summed over all domains. */
+long long vans_batch_cells(vans_t h);
+
+/* ---------------------------------------------------------------- misc --- */
+
+/* Total cells of the handle (single domain: nx*ny*nz). */
+long long vans_cells(vans_t h);
+
+/* Number of kernel launches this handle has enqueued so far (graph replays
+ * count every kernel node they contain). */
+long long vans_launch_count(vans_t h);
+
+/* Check the current state for non-finite values or |u| >= 0.5 (Mach ~0.9);
+ * returns VANS_OK or VANS_ERR_DIVERGED.  Synchronises. */
+int vans_check(vans_t h);
+
+const char *vans_status_string(int status);
+const char *vans_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VANS_H */

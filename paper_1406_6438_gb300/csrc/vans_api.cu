@@ -1,0 +1,713 @@
+// vans_api.cu -- host runtime behind the C ABI of include/vans.h: parameter
+// validation, workspace layout, the ping-pong state, CUDA-graph replay of long
+// step sequences, the launch-configuration autotuner and the batched tile list.
+// The library allocates no device memory: everything lives in the caller's
+// workspace.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "vans.h"
+#include "vans_internal.h"
+
+using vans::Launch;
+using vans::Tile;
+using vans::VDom;
+
+namespace {
+
+constexpr int kGraphSteps = 64;   // steps per captured graph (even: parity is restored)
+
+long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
+
+int pitch_for(int nx) { return (int)round_up(VANS_OFF + round_up(nx, 128) + 1, 32); }
+
+// floats of one state buffer (Q planes of rows*pitch), rounded to 256 bytes
+long long state_floats_of(int q, int nx, int ny, int nz) {
+    const long long plane = (long long)ny * nz * pitch_for(nx);
+    return round_up((long long)q * plane, 64);
+}
+
+long long eps_floats_of(int nx, int ny, int nz) {
+    return round_up((long long)ny * nz * pitch_for(nx), 64);
+}
+
+constexpr long long kFlagFloats = 64;   // 256 bytes of status words
+
+int validate(const vans_params *p, bool batched) {
+    if (!p) return VANS_ERR_ARG;
+    if (p->q != 9 && p->q != 19) return VANS_ERR_ARG;
+    if (batched && p->q != 9) return VANS_ERR_UNSUPPORTED;
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) return VANS_ERR_ARG;
+    if (p->q == 9 && p->nz != 1) return VANS_ERR_ARG;
+    if (p->wall_mask & ~7) return VANS_ERR_ARG;
+    if (p->wall_mask & 1) return VANS_ERR_UNSUPPORTED;
+    if (p->q == 9 && (p->wall_mask & 4)) return VANS_ERR_ARG;
+    if (!(p->tau > 0.5f) || !isfinite(p->tau)) return VANS_ERR_ARG;
+    for (int k = 0; k < 3; ++k)
+        if (!isfinite(p->g[k])) return VANS_ERR_ARG;
+    if (p->drag_mode < 0 || p->drag_mode > 2) return VANS_ERR_ARG;
+    if (p->k_mode < 0 || p->k_mode > 2) return VANS_ERR_ARG;
+    if (p->drag_mode != 0) {
+        if (p->k_mode == 0 && !(p->d_p > 0.f && isfinite(p->d_p))) return VANS_ERR_ARG;
+        if (p->k_mode != 0 && !(p->K > 0.f && isfinite(p->K))) return VANS_ERR_ARG;
+        if (p->k_mode == 1 && !(p->F_eps >= 0.f && isfinite(p->F_eps))) return VANS_ERR_ARG;
+    }
+    // index arithmetic limits: rows and columns are int, offsets 64-bit
+    const long long rows = (long long)p->ny * p->nz;
+    if (rows > (1LL << 30) || p->nx > (1 << 28)) return VANS_ERR_ARG;
+    return VANS_OK;
+}
+
+// Host-side constants of the drag law: alpha = ca * a(eps), beta = cb * b(eps).
+void fill_dom(const vans_params *p, VDom &d) {
+    memset(&d, 0, sizeof(d));
+    d.q = p->q;
+    d.nx = p->nx;
+    d.ny = p->ny;
+    d.nz = p->nz;
+    d.rows = p->ny * p->nz;
+    d.pitch = pitch_for(p->nx);
+    d.plane = (long long)d.rows * d.pitch;
+    d.wall_y = (p->wall_mask >> 1) & 1;
+    d.wall_z = (p->wall_mask >> 2) & 1;
+    const double tau = p->tau;
+    d.omega = (float)(1.0 / tau);
+    d.ctau = (float)(1.0 - 0.5 / tau);
+    d.g[0] = p->g[0];
+    d.g[1] = p->g[1];
+    d.g[2] = (p->q == 19) ? p->g[2] : 0.f;
+    d.drag_mode = p->drag_mode;
+    d.k_mode = p->k_mode;
+    const double nu = (tau - 0.5) / 3.0;        // nu = cs^2 (tau - 1/2)
+    if (p->k_mode == 0) {
+        d.ca = (float)(150.0 * nu / ((double)p->d_p * p->d_p));
+        d.cb = (float)(1.75 / p->d_p);
+    } else if (p->k_mode == 1) {
+        d.ca = (float)(nu / p->K);
+        d.cb = (float)(p->F_eps / sqrt((double)p->K));
+    } else {
+        d.ca = (float)(nu / p->K);
+        d.cb = (float)(1.75 / sqrt(150.0 * p->K));
+    }
+    d.cells = (long long)p->nx * p->ny * p->nz;
+}
+
+bool launch_ok(const vans_launch *c) {
+    if (!c) return false;
+    if (c->cpt != 1 && c->cpt != 2 && c->cpt != 4) return false;
+    if (c->warps < 1 || c->warps > 8 || c->rows < 1 || c->rows > 8) return false;
+    return c->warps * c->rows <= 8;
+}
+
+}  // namespace
+
+struct vans_s {
+    bool batched = false;
+    int q = 9;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr;                 // private stream for graph capture
+    int device = 0;
+    long long launches = 0;
+    Launch L{4, 4, 1};
+    cudaGraphExec_t gexec = nullptr;
+    int *flag = nullptr;                        // device status words (workspace)
+    // single domain
+    vans_params p{};
+    VDom dom{};
+    float *st[2] = {nullptr, nullptr};
+    int cur = 0;
+    float *eps_pad = nullptr;
+    bool eps_set = false;
+    long long sfloats = 0;
+    // batched
+    int n = 0;
+    std::vector<vans_params> bp;
+    std::vector<VDom> doms;                     // host copy of the device table
+    VDom *doms_d = nullptr;
+    Tile *tiles_d = nullptr;
+    long long tile_cap = 0;
+    std::vector<Tile> tiles;
+    int grid = 0;
+    int parity = 0;
+    std::vector<char> dom_ready;
+};
+
+namespace {
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? VANS_OK : VANS_ERR_CUDA; }
+
+void drop_graph(vans_t h) {
+    if (h->gexec) {
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+    }
+}
+
+cudaError_t one_step(vans_t h, cudaStream_t s, int par) {
+    ++h->launches;
+    if (h->batched)
+        return vans::launch_step_batched(h->doms_d, h->tiles_d, (int)h->tiles.size(), par, h->L,
+                                         h->grid, s);
+    return vans::launch_step(h->q, h->dom, h->st[par], h->st[par ^ 1], h->L, s);
+}
+
+int ensure_graph(vans_t h) {
+    if (h->gexec) return VANS_OK;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return VANS_ERR_CUDA;
+    const long long before = h->launches;
+    cudaError_t le = cudaSuccess;
+    for (int s = 0; s < kGraphSteps && le == cudaSuccess; ++s) le = one_step(h, h->cap, s & 1);
+    h->launches = before;                       // capture does not run anything
+    e = cudaStreamEndCapture(h->cap, &g);
+    if (le != cudaSuccess || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return VANS_ERR_CUDA;
+    }
+    e = cudaGraphInstantiate(&h->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        h->gexec = nullptr;
+        return VANS_ERR_CUDA;
+    }
+    return VANS_OK;
+}
+
+// nsteps steps; the parity lives in h->cur (single) or h->parity (batched)
+int run_steps(vans_t h, int nsteps) {
+    int &par = h->batched ? h->parity : h->cur;
+    int left = nsteps;
+    if (left >= kGraphSteps) {
+        if (par != 0) {
+            if (one_step(h, h->stream, par) != cudaSuccess) return VANS_ERR_CUDA;
+            par ^= 1;
+            --left;
+        }
+        if (left >= kGraphSteps) {
+            int rc = ensure_graph(h);
+            if (rc) return rc;
+            while (left >= kGraphSteps) {
+                if (cudaGraphLaunch(h->gexec, h->stream) != cudaSuccess) return VANS_ERR_CUDA;
+                h->launches += kGraphSteps;
+                left -= kGraphSteps;
+            }
+        }
+    }
+    while (left > 0) {
+        if (one_step(h, h->stream, par) != cudaSuccess) return VANS_ERR_CUDA;
+        par ^= 1;
+        --left;
+    }
+    return VANS_OK;
+}
+
+int make_streams(vans_t h, void *stream) {
+    h->stream = (cudaStream_t)stream;
+    if (cudaGetDevice(&h->device) != cudaSuccess) return VANS_ERR_CUDA;
+    if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) return VANS_ERR_CUDA;
+    return VANS_OK;
+}
+
+// read and clear the status word; synchronises the stream
+int read_flag(vans_t h, int *value) {
+    int v = 0;
+    if (cudaMemcpyAsync(&v, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+        return VANS_ERR_CUDA;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return VANS_ERR_CUDA;
+    *value = v;
+    return VANS_OK;
+}
+
+void build_tiles(vans_t h, const Launch &L, std::vector<Tile> &out) {
+    out.clear();
+    const int bx = 32 * L.cpt * L.warps;
+    for (int d = 0; d < h->n; ++d) {
+        const VDom &D = h->doms[d];
+        for (int r = 0; r < D.rows; r += L.rows)
+            for (int x = 0; x < D.nx; x += bx) out.push_back(Tile{d, r, x, 0});
+    }
+}
+
+int set_batch_launch(vans_t h, const Launch &L) {
+    std::vector<Tile> t;
+    build_tiles(h, L, t);
+    if ((long long)t.size() > h->tile_cap) return VANS_ERR_ARG;
+    if (cudaMemcpyAsync(h->tiles_d, t.data(), t.size() * sizeof(Tile), cudaMemcpyHostToDevice,
+                        h->stream) != cudaSuccess)
+        return VANS_ERR_CUDA;
+    h->tiles.swap(t);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (sms <= 0) sms = 1;
+    h->grid = sms * vans::batched_blocks_per_sm(L);
+    h->L = L;
+    drop_graph(h);
+    return VANS_OK;
+}
+
+template <class F>
+float time_launches(vans_t h, F &&fn, int reps) {
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    for (int i = 0; i < 2; ++i) fn();
+    cudaEventRecord(a, h->stream);
+    for (int i = 0; i < reps; ++i) fn();
+    cudaEventRecord(b, h->stream);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    if (cudaGetLastError() != cudaSuccess) ms = 1e30f;
+    else cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return ms;
+}
+
+std::vector<Launch> candidates(int q) {
+    std::vector<Launch> c;
+    const int cpts[3] = {1, 2, 4};
+    for (int cpt : cpts)
+        for (int warps = 1; warps <= 8; warps *= 2)
+            for (int rows = 1; rows <= 4; rows *= 2) {
+                if (warps * rows > 8 || warps * rows < 2) continue;
+                if (q == 19 && cpt == 4 && warps * rows > 4) continue;
+                c.push_back(Launch{cpt, warps, rows});
+            }
+    return c;
+}
+
+}  // namespace
+
+// ===================================================================== ABI ==
+extern "C" {
+
+long long vans_state_floats(const vans_params *p) {
+    if (validate(p, false) != VANS_OK) return -1;
+    return state_floats_of(p->q, p->nx, p->ny, p->nz);
+}
+
+size_t vans_workspace_bytes(const vans_params *p) {
+    if (validate(p, false) != VANS_OK) return 0;
+    const long long f = 2 * state_floats_of(p->q, p->nx, p->ny, p->nz) +
+                        eps_floats_of(p->nx, p->ny, p->nz) + kFlagFloats;
+    return (size_t)f * sizeof(float);
+}
+
+int vans_create(const vans_params *p, void *workspace, size_t workspace_bytes, void *cuda_stream,
+                vans_t *out) {
+    if (!out) return VANS_ERR_ARG;
+    *out = nullptr;
+    const int v = validate(p, false);
+    if (v) return v;
+    if (!workspace || ((uintptr_t)workspace & 255)) return VANS_ERR_ARG;
+    if (workspace_bytes < vans_workspace_bytes(p)) return VANS_ERR_ARG;
+    vans_t h = new (std::nothrow) vans_s();
+    if (!h) return VANS_ERR_ARG;
+    h->q = p->q;
+    h->p = *p;
+    fill_dom(p, h->dom);
+    h->sfloats = state_floats_of(p->q, p->nx, p->ny, p->nz);
+    float *w = (float *)workspace;
+    h->st[0] = w;
+    h->st[1] = w + h->sfloats;
+    h->eps_pad = w + 2 * h->sfloats;
+    h->flag = (int *)(h->eps_pad + eps_floats_of(p->nx, p->ny, p->nz));
+    h->dom.eps = h->eps_pad;
+    h->L = (p->q == 9) ? Launch{4, 4, 1} : Launch{2, 4, 1};
+    int rc = make_streams(h, cuda_stream);
+    if (rc) {
+        vans_destroy(h);
+        return rc;
+    }
+    // a defined padding (1.0 porosity, zero deviations) for lanes past nx
+    if (cudaMemsetAsync(workspace, 0, vans_workspace_bytes(p), h->stream) != cudaSuccess) {
+        vans_destroy(h);
+        return VANS_ERR_CUDA;
+    }
+    *out = h;
+    return VANS_OK;
+}
+
+void vans_destroy(vans_t h) {
+    if (!h) return;
+    drop_graph(h);
+    if (h->cap) cudaStreamDestroy(h->cap);
+    delete h;
+}
+
+int vans_set_eps(vans_t h, const float *eps_dev) {
+    if (!h || h->batched || !eps_dev) return VANS_ERR_ARG;
+    if (cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream) != cudaSuccess) return VANS_ERR_CUDA;
+    ++h->launches;
+    if (vans::launch_pad_eps(h->dom, eps_dev, nullptr, h->flag, h->stream) != cudaSuccess)
+        return VANS_ERR_CUDA;
+    int bad = 0;
+    int rc = read_flag(h, &bad);
+    if (rc) return rc;
+    if (bad) return VANS_ERR_ARG;
+    ++h->launches;
+    if (vans::launch_pad_eps(h->dom, eps_dev, h->eps_pad, h->flag, h->stream) != cudaSuccess)
+        return VANS_ERR_CUDA;
+    if (cudaMemsetAsync(h->st[0], 0, 2 * h->sfloats * sizeof(float), h->stream) != cudaSuccess)
+        return VANS_ERR_CUDA;
+    h->cur = 0;
+    h->eps_set = true;
+    return VANS_OK;
+}
+
+int vans_step(vans_t h, int nsteps) {
+    if (!h || h->batched || nsteps < 0) return VANS_ERR_ARG;
+    if (!h->eps_set) return VANS_ERR_STATE;
+    return run_steps(h, nsteps);
+}
+
+int vans_step_raw(vans_t h, const float *in, float *out) {
+    if (!h || h->batched || !in || !out || in == out) return VANS_ERR_ARG;
+    if (!h->eps_set) return VANS_ERR_STATE;
+    ++h->launches;
+    return cuda_status(vans::launch_step(h->q, h->dom, in, out, h->L, h->stream));
+}
+
+int vans_moments(vans_t h, float *rho_dev, float *u_dev) {
+    if (!h || h->batched) return VANS_ERR_ARG;
+    if (!h->eps_set) return VANS_ERR_STATE;
+    if (!rho_dev && !u_dev) return VANS_OK;
+    ++h->launches;
+    return cuda_status(vans::launch_moments(h->q, h->dom, h->st[h->cur], rho_dev, u_dev, h->stream));
+}
+
+int vans_get_populations(vans_t h, float *f_dev) {
+    if (!h || h->batched || !f_dev) return VANS_ERR_ARG;
+    if (!h->eps_set) return VANS_ERR_STATE;
+    ++h->launches;
+    return cuda_status(vans::launch_export(h->q, h->dom, h->st[h->cur], f_dev, h->stream));
+}
+
+int vans_set_populations(vans_t h, const float *f_dev) {
+    if (!h || h->batched || !f_dev) return VANS_ERR_ARG;
+    if (!h->eps_set) return VANS_ERR_STATE;
+    ++h->launches;
+    return cuda_status(vans::launch_import(h->q, h->dom, f_dev, h->st[h->cur], h->stream));
+}
+
+int vans_get_state(vans_t h, float *state_dev) {
+    if (!h || h->batched || !state_dev) return VANS_ERR_ARG;
+    if (!h->eps_set) return VANS_ERR_STATE;
+    return cuda_status(cudaMemcpyAsync(state_dev, h->st[h->cur], h->sfloats * sizeof(float),
+                                       cudaMemcpyDeviceToDevice, h->stream));
+}
+
+int vans_set_state(vans_t h, const float *state_dev) {
+    if (!h || h->batched || !state_dev) return VANS_ERR_ARG;
+    if (!h->eps_set) return VANS_ERR_STATE;
+    return cuda_status(cudaMemcpyAsync(h->st[h->cur], state_dev, h->sfloats * sizeof(float),
+                                       cudaMemcpyDeviceToDevice, h->stream));
+}
+
+int vans_get_launch(vans_t h, vans_launch *cfg) {
+    if (!h || !cfg) return VANS_ERR_ARG;
+    cfg->cpt = h->L.cpt;
+    cfg->warps = h->L.warps;
+    cfg->rows = h->L.rows;
+    return VANS_OK;
+}
+
+int vans_set_launch(vans_t h, const vans_launch *cfg) {
+    if (!h || !launch_ok(cfg)) return VANS_ERR_ARG;
+    const Launch L{cfg->cpt, cfg->warps, cfg->rows};
+    if (h->batched) return set_batch_launch(h, L);
+    h->L = L;
+    drop_graph(h);
+    return VANS_OK;
+}
+
+int vans_autotune(vans_t h, vans_launch *chosen) {
+    if (!h || h->batched) return VANS_ERR_ARG;
+    if (!h->eps_set) return VANS_ERR_STATE;
+    // time each candidate on the current state; the output goes to the other
+    // buffer, which holds nothing live, so the state is unchanged
+    const std::vector<Launch> cs = candidates(h->q);
+    Launch best = h->L;
+    float best_ms = 1e30f;
+    const float *in = h->st[h->cur];
+    float *outb = h->st[h->cur ^ 1];
+    const int reps = h->dom.cells > (1 << 22) ? 5 : 20;
+    for (const Launch &L : cs) {
+        const float ms = time_launches(
+            h, [&] { vans::launch_step(h->q, h->dom, in, outb, L, h->stream); }, reps);
+        h->launches += reps + 2;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = L;
+        }
+    }
+    if (cudaGetLastError() != cudaSuccess) return VANS_ERR_CUDA;
+    h->L = best;
+    drop_graph(h);
+    if (chosen) {
+        chosen->cpt = best.cpt;
+        chosen->warps = best.warps;
+        chosen->rows = best.rows;
+    }
+    return VANS_OK;
+}
+
+int vans_flux(vans_t h, const float *state, int x_out, float *J_dev) {
+    if (!h || h->batched || !J_dev) return VANS_ERR_ARG;
+    if (!h->eps_set) return VANS_ERR_STATE;
+    if (x_out < 0 || x_out >= h->dom.nx) return VANS_ERR_ARG;
+    ++h->launches;
+    return cuda_status(
+        vans::launch_flux(h->q, h->dom, state ? state : h->st[h->cur], x_out, J_dev, h->stream));
+}
+
+int vans_flux_seed(vans_t h, const float *state, int x_out, float *lam_dev, float *grad_acc) {
+    if (!h || h->batched || !lam_dev || !grad_acc) return VANS_ERR_ARG;
+    if (!h->eps_set) return VANS_ERR_STATE;
+    if (x_out < 0 || x_out >= h->dom.nx) return VANS_ERR_ARG;
+    const int D = h->q == 9 ? 2 : 3;
+    if (cudaMemsetAsync(lam_dev, 0, h->sfloats * sizeof(float), h->stream) != cudaSuccess)
+        return VANS_ERR_CUDA;
+    if (cudaMemsetAsync(grad_acc, 0, (1 + D) * h->dom.cells * sizeof(float), h->stream) != cudaSuccess)
+        return VANS_ERR_CUDA;
+    ++h->launches;
+    return cuda_status(vans::launch_flux_seed(h->q, h->dom, state ? state : h->st[h->cur], x_out,
+                                              lam_dev, grad_acc, h->stream));
+}
+
+int vans_step_adjoint(vans_t h, const float *state_t, const float *lam_in, float *lam_out,
+                      float *grad_acc) {
+    if (!h || h->batched || !state_t || !lam_in || !lam_out || !grad_acc) return VANS_ERR_ARG;
+    if (lam_in == lam_out || (const float *)lam_out == state_t) return VANS_ERR_ARG;
+    if (!h->eps_set) return VANS_ERR_STATE;
+    ++h->launches;
+    return cuda_status(
+        vans::launch_step_adjoint(h->q, h->dom, state_t, lam_in, lam_out, grad_acc, h->stream));
+}
+
+int vans_grad_finalize(vans_t h, const float *lam0, const float *grad_acc, float *dJdeps_dev) {
+    if (!h || h->batched || !lam0 || !grad_acc || !dJdeps_dev) return VANS_ERR_ARG;
+    if (!h->eps_set) return VANS_ERR_STATE;
+    ++h->launches;
+    return cuda_status(
+        vans::launch_grad_finalize(h->q, h->dom, lam0, grad_acc, dJdeps_dev, h->stream));
+}
+
+int vans_check(vans_t h) {
+    if (!h) return VANS_ERR_ARG;
+    if (cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream) != cudaSuccess) return VANS_ERR_CUDA;
+    if (h->batched) {
+        for (int d = 0; d < h->n; ++d) {
+            if (!h->dom_ready[d]) continue;
+            ++h->launches;
+            if (vans::launch_check(9, h->doms[d], h->doms[d].f[h->parity], h->flag, h->stream) !=
+                cudaSuccess)
+                return VANS_ERR_CUDA;
+        }
+    } else {
+        if (!h->eps_set) return VANS_ERR_STATE;
+        ++h->launches;
+        if (vans::launch_check(h->q, h->dom, h->st[h->cur], h->flag, h->stream) != cudaSuccess)
+            return VANS_ERR_CUDA;
+    }
+    int bad = 0;
+    int rc = read_flag(h, &bad);
+    if (rc) return rc;
+    return bad ? VANS_ERR_DIVERGED : VANS_OK;
+}
+
+long long vans_cells(vans_t h) {
+    if (!h) return -1;
+    if (h->batched) return vans_batch_cells(h);
+    return h->dom.cells;
+}
+
+long long vans_launch_count(vans_t h) { return h ? h->launches : -1; }
+
+// ------------------------------------------------------------- batched ----
+
+static long long batch_tile_cap(const vans_params *p, int n) {
+    long long t = 0;   // the smallest tile the autotuner may pick: 32 cells x 1 row
+    for (int d = 0; d < n; ++d) t += (long long)p[d].ny * ((p[d].nx + 31) / 32);
+    return t;
+}
+
+size_t vans_batch_workspace_bytes(const vans_params *p, int n) {
+    if (!p || n < 1) return 0;
+    long long bytes = round_up((long long)n * sizeof(VDom), 256) +
+                      round_up(batch_tile_cap(p, n) * (long long)sizeof(Tile), 256);
+    for (int d = 0; d < n; ++d) {
+        if (validate(&p[d], true) != VANS_OK) return 0;
+        bytes += (2 * state_floats_of(9, p[d].nx, p[d].ny, 1) + eps_floats_of(p[d].nx, p[d].ny, 1)) *
+                 (long long)sizeof(float);
+    }
+    bytes += kFlagFloats * sizeof(float);
+    return (size_t)bytes;
+}
+
+int vans_batch_create(const vans_params *p, int n, void *workspace, size_t workspace_bytes,
+                      void *cuda_stream, vans_t *out) {
+    if (!out) return VANS_ERR_ARG;
+    *out = nullptr;
+    if (!p || n < 1) return VANS_ERR_ARG;
+    for (int d = 0; d < n; ++d) {
+        const int v = validate(&p[d], true);
+        if (v) return v;
+    }
+    if (!workspace || ((uintptr_t)workspace & 255)) return VANS_ERR_ARG;
+    const size_t need = vans_batch_workspace_bytes(p, n);
+    if (need == 0 || workspace_bytes < need) return VANS_ERR_ARG;
+    vans_t h = new (std::nothrow) vans_s();
+    if (!h) return VANS_ERR_ARG;
+    h->batched = true;
+    h->q = 9;
+    h->n = n;
+    h->bp.assign(p, p + n);
+    char *w = (char *)workspace;
+    h->doms_d = (VDom *)w;
+    w += round_up((long long)n * sizeof(VDom), 256);
+    h->tiles_d = (Tile *)w;
+    h->tile_cap = batch_tile_cap(p, n);
+    w += round_up(h->tile_cap * (long long)sizeof(Tile), 256);
+    h->doms.resize(n);
+    long long dense = 0;
+    for (int d = 0; d < n; ++d) {
+        VDom &D = h->doms[d];
+        fill_dom(&p[d], D);
+        const long long sf = state_floats_of(9, p[d].nx, p[d].ny, 1);
+        D.f[0] = (float *)w;
+        D.f[1] = (float *)w + sf;
+        D.eps = (float *)w + 2 * sf;
+        D.dense_off = dense;
+        dense += D.cells;
+        w += (2 * sf + eps_floats_of(p[d].nx, p[d].ny, 1)) * sizeof(float);
+    }
+    h->flag = (int *)w;
+    h->dom_ready.assign(n, 0);
+    int rc = make_streams(h, cuda_stream);
+    if (rc) {
+        vans_destroy(h);
+        return rc;
+    }
+    if (cudaMemsetAsync(workspace, 0, need, h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(h->doms_d, h->doms.data(), n * sizeof(VDom), cudaMemcpyHostToDevice,
+                        h->stream) != cudaSuccess) {
+        vans_destroy(h);
+        return VANS_ERR_CUDA;
+    }
+    rc = set_batch_launch(h, Launch{4, 4, 1});
+    if (rc) {
+        vans_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return VANS_OK;
+}
+
+int vans_batch_set_eps(vans_t h, int d, const float *eps_dev) {
+    if (!h || !h->batched || d < 0 || d >= h->n || !eps_dev) return VANS_ERR_ARG;
+    const VDom &D = h->doms[d];
+    if (cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream) != cudaSuccess) return VANS_ERR_CUDA;
+    ++h->launches;
+    if (vans::launch_pad_eps(D, eps_dev, nullptr, h->flag, h->stream) != cudaSuccess)
+        return VANS_ERR_CUDA;
+    int bad = 0;
+    int rc = read_flag(h, &bad);
+    if (rc) return rc;
+    if (bad) return VANS_ERR_ARG;
+    ++h->launches;
+    if (vans::launch_pad_eps(D, eps_dev, (float *)D.eps, h->flag, h->stream) != cudaSuccess)
+        return VANS_ERR_CUDA;
+    const long long sf = state_floats_of(9, D.nx, D.ny, 1);
+    if (cudaMemsetAsync(D.f[0], 0, 2 * sf * sizeof(float), h->stream) != cudaSuccess)
+        return VANS_ERR_CUDA;
+    h->dom_ready[d] = 1;
+    return VANS_OK;
+}
+
+int vans_batch_step(vans_t h, int nsteps) {
+    if (!h || !h->batched || nsteps < 0) return VANS_ERR_ARG;
+    for (int d = 0; d < h->n; ++d)
+        if (!h->dom_ready[d]) return VANS_ERR_STATE;
+    return run_steps(h, nsteps);
+}
+
+int vans_batch_moments(vans_t h, int d, float *rho_dev, float *u_dev) {
+    if (!h || !h->batched || d < 0 || d >= h->n) return VANS_ERR_ARG;
+    if (!h->dom_ready[d]) return VANS_ERR_STATE;
+    if (!rho_dev && !u_dev) return VANS_OK;
+    ++h->launches;
+    return cuda_status(vans::launch_moments(9, h->doms[d], h->doms[d].f[h->parity], rho_dev, u_dev,
+                                            h->stream));
+}
+
+int vans_batch_get_populations(vans_t h, int d, float *f_dev) {
+    if (!h || !h->batched || d < 0 || d >= h->n || !f_dev) return VANS_ERR_ARG;
+    if (!h->dom_ready[d]) return VANS_ERR_STATE;
+    ++h->launches;
+    return cuda_status(vans::launch_export(9, h->doms[d], h->doms[d].f[h->parity], f_dev, h->stream));
+}
+
+int vans_batch_autotune(vans_t h, vans_launch *chosen) {
+    if (!h || !h->batched) return VANS_ERR_ARG;
+    for (int d = 0; d < h->n; ++d)
+        if (!h->dom_ready[d]) return VANS_ERR_STATE;
+    const Launch keep = h->L;
+    Launch best = keep;
+    float best_ms = 1e30f;
+    const int par = h->parity;
+    for (const Launch &L : candidates(9)) {
+        if (set_batch_launch(h, L) != VANS_OK) continue;
+        // reads the current parity and writes the other buffer of every domain
+        const float ms = time_launches(
+            h,
+            [&] {
+                vans::launch_step_batched(h->doms_d, h->tiles_d, (int)h->tiles.size(), par, h->L,
+                                          h->grid, h->stream);
+            },
+            5);
+        h->launches += 7;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = L;
+        }
+    }
+    int rc = set_batch_launch(h, best);
+    if (rc) return rc;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return VANS_ERR_CUDA;
+    if (chosen) {
+        chosen->cpt = best.cpt;
+        chosen->warps = best.warps;
+        chosen->rows = best.rows;
+    }
+    return VANS_OK;
+}
+
+long long vans_batch_cells(vans_t h) {
+    if (!h || !h->batched) return -1;
+    long long c = 0;
+    for (const VDom &D : h->doms) c += D.cells;
+    return c;
+}
+
+const char *vans_status_string(int status) {
+    switch (status) {
+        case VANS_OK: return "ok";
+        case VANS_ERR_ARG: return "invalid argument";
+        case VANS_ERR_CUDA: return "CUDA error";
+        case VANS_ERR_DIVERGED: return "state diverged (non-finite or |u| >= 0.5)";
+        case VANS_ERR_TIMEOUT: return "device wait timed out";
+        case VANS_ERR_UNSUPPORTED: return "unsupported configuration";
+        case VANS_ERR_STATE: return "call out of order";
+        default: return "unknown status";
+    }
+}
+
+const char *vans_version(void) { return "vans-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

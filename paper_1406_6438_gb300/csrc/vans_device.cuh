@@ -1,0 +1,367 @@
+// vans_device.cuh -- device-side building blocks of the porous LBM step.
+//
+// State layout.  One state buffer holds Q planes, one per direction i; a plane
+// holds rows = ny*nz padded rows of `pitch` floats (pitch is a multiple of 32
+// floats, so every row starts on a 128-byte boundary).  Column c of a row lives
+// at row + VANS_OFF + c for c in [-1, nx]: columns -1 and nx are halo copies
+// that make the periodic x wrap free for the pull.  What a plane stores for cell
+// x is the post-collision population of direction i of the previous step, as a
+// deviation from w_i * eps~(x + e_i), the porosity of the cell it streams to
+// (eps~ = eps(x) when that cell lies past a wall).  The pull then reads exactly
+// the deviation h_i = f_i - w_i eps(x) of the receiving cell, and the rest
+// state f = w eps is stored as all zeros.  Deviations are O(1e-3) of f, so FP32
+// keeps about 3 more decimal digits of the flow than it would on raw f.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "vans_internal.h"
+
+#define VANS_FULL 0xffffffffu
+
+namespace vans {
+
+// ------------------------------------------------------------ lattices ----
+// D2Q9 and D3Q19 velocity sets and weights (Qian, d'Humieres & Lallemand 1992,
+// the lattice family of Eq. d2q9eq), in the direction order of vans.h.
+template <int Q> struct Lat;
+
+template <> struct Lat<9> {
+    static constexpr int D = 2;
+    __host__ __device__ static constexpr int ex(int i) {
+        return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+    }
+    __host__ __device__ static constexpr int ey(int i) {
+        return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+    }
+    __host__ __device__ static constexpr int ez(int) { return 0; }
+    __host__ __device__ static constexpr int opp(int i) {
+        return i == 0 ? 0 : (i <= 4 ? (i + 1) % 4 + 1 : (i - 3) % 4 + 5);
+    }
+    __host__ __device__ static constexpr float w(int i) {
+        return i == 0 ? 4.0f / 9.0f : (i <= 4 ? 1.0f / 9.0f : 1.0f / 36.0f);
+    }
+};
+
+template <> struct Lat<19> {
+    static constexpr int D = 3;
+    // 0 rest; 1..6 faces (+x,-x,+y,-y,+z,-z); 7..18 edges in opposite pairs
+    __host__ __device__ static constexpr int ex(int i) {
+        return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1
+             : ((i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0);
+    }
+    __host__ __device__ static constexpr int ey(int i) {
+        return (i == 3 || i == 7 || i == 10 || i == 15 || i == 17) ? 1
+             : ((i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1 : 0);
+    }
+    __host__ __device__ static constexpr int ez(int i) {
+        return (i == 5 || i == 11 || i == 14 || i == 15 || i == 18) ? 1
+             : ((i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0);
+    }
+    __host__ __device__ static constexpr int opp(int i) {
+        return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1);
+    }
+    __host__ __device__ static constexpr float w(int i) {
+        return i == 0 ? 1.0f / 3.0f : (i <= 6 ? 1.0f / 18.0f : 1.0f / 36.0f);
+    }
+};
+
+// ------------------------------------------------------- vector memory ----
+template <int CPT> struct Vec;
+template <> struct Vec<1> { using T = float; };
+template <> struct Vec<2> { using T = float2; };
+template <> struct Vec<4> { using T = float4; };
+
+template <int CPT>
+__device__ __forceinline__ void ld_vec(const float *p, float v[CPT]) {
+    if constexpr (CPT == 4) {
+        const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    } else if constexpr (CPT == 2) {
+        const float2 t = __ldg(reinterpret_cast<const float2 *>(p));
+        v[0] = t.x; v[1] = t.y;
+    } else {
+        v[0] = __ldg(p);
+    }
+}
+
+template <int CPT>
+__device__ __forceinline__ void st_vec(float *p, const float v[CPT]) {
+    if constexpr (CPT == 4) {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    } else if constexpr (CPT == 2) {
+        *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+    } else {
+        *p = v[0];
+    }
+}
+
+// Values at columns x0+s .. x0+s+CPT-1 of a row (row points at column 0),
+// s in {-1, 0, +1} and the same for the whole warp.  One aligned vector load per
+// lane; the value that crosses into the neighbouring lane comes by shuffle and
+// the warp's edge lanes fetch theirs with one scalar load.  All 32 lanes must
+// take part.
+template <int CPT>
+__device__ __forceinline__ void ld_shift(const float *__restrict__ row, int x0, int s, int lane,
+                                         float v[CPT]) {
+    float a[CPT];
+    ld_vec<CPT>(row + x0, a);
+    if (s == 0) {
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) v[k] = a[k];
+    } else if (s < 0) {
+        float left = __shfl_up_sync(VANS_FULL, a[CPT - 1], 1);
+        if (lane == 0) left = __ldg(row + x0 - 1);
+        v[0] = left;
+#pragma unroll
+        for (int k = 1; k < CPT; ++k) v[k] = a[k - 1];
+    } else {
+        float right = __shfl_down_sync(VANS_FULL, a[0], 1);
+        if (lane == 31) right = __ldg(row + x0 + CPT);
+#pragma unroll
+        for (int k = 0; k < CPT - 1; ++k) v[k] = a[k + 1];
+        v[CPT - 1] = right;
+    }
+}
+
+// Columns x0-1 .. x0+CPT of a row (the cells plus one neighbour on each side).
+template <int CPT>
+__device__ __forceinline__ void ld_ext(const float *__restrict__ row, int x0, int lane,
+                                       float v[CPT + 2]) {
+    float a[CPT];
+    ld_vec<CPT>(row + x0, a);
+    float left = __shfl_up_sync(VANS_FULL, a[CPT - 1], 1);
+    float right = __shfl_down_sync(VANS_FULL, a[0], 1);
+    if (lane == 0) left = __ldg(row + x0 - 1);
+    if (lane == 31) right = __ldg(row + x0 + CPT);
+    v[0] = left;
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) v[k + 1] = a[k];
+    v[CPT + 1] = right;
+}
+
+// Store cells x0..x0+CPT-1 of a row, skipping columns >= nx.
+template <int CPT>
+__device__ __forceinline__ void st_masked(float *row, int x0, int nx, const float v[CPT]) {
+    if (x0 + CPT <= nx) {
+        st_vec<CPT>(row + x0, v);
+    } else {
+#pragma unroll
+        for (int k = 0; k < CPT; ++k)
+            if (x0 + k < nx) row[x0 + k] = v[k];
+    }
+}
+
+// Inverse of ld_shift: value v[k] of cell x0+k goes to column x0+k+s.  Lanes
+// compose aligned vectors with a shuffle; the value that crosses into the next
+// warp is written by a scalar store.  Cells past nx write into columns that no
+// pull reads, so no mask is needed.
+template <int CPT>
+__device__ __forceinline__ void st_shift(float *row, int x0, int s, int lane, const float v[CPT]) {
+    if (s == 0) {
+        st_vec<CPT>(row + x0, v);
+    } else if (s < 0) {
+        const float nxt = __shfl_down_sync(VANS_FULL, v[0], 1);
+        if (lane != 31) {
+            float a[CPT];
+#pragma unroll
+            for (int k = 0; k < CPT - 1; ++k) a[k] = v[k + 1];
+            a[CPT - 1] = nxt;
+            st_vec<CPT>(row + x0, a);
+        } else {
+#pragma unroll
+            for (int k = 0; k < CPT - 1; ++k) row[x0 + k] = v[k + 1];
+        }
+        if (lane == 0) row[x0 - 1] = v[0];
+    } else {
+        const float prv = __shfl_up_sync(VANS_FULL, v[CPT - 1], 1);
+        if (lane != 0) {
+            float a[CPT];
+            a[0] = prv;
+#pragma unroll
+            for (int k = 1; k < CPT; ++k) a[k] = v[k - 1];
+            st_vec<CPT>(row + x0, a);
+        } else {
+#pragma unroll
+            for (int k = 0; k < CPT - 1; ++k) row[x0 + 1 + k] = v[k];
+        }
+        if (lane == 31) row[x0 + CPT] = v[CPT - 1];
+    }
+}
+
+// ------------------------------------------------------- row neighbours ----
+// Neighbour row indices along y (or z) at offsets -1, 0, +1 and whether that
+// neighbour lies past a bounce-back wall.  Periodic axes wrap.
+struct Nb3 {
+    int r[3];
+    bool wall[3];
+};
+
+template <bool EDGE>
+__device__ __forceinline__ Nb3 nb3(int c, int n, int walls) {
+    Nb3 o;
+    o.r[1] = c;
+    o.wall[1] = false;
+    if (EDGE) {
+        o.r[0] = (c == 0) ? n - 1 : c - 1;
+        o.r[2] = (c == n - 1) ? 0 : c + 1;
+        o.wall[0] = walls && c == 0;
+        o.wall[2] = walls && c == n - 1;
+    } else {
+        o.r[0] = c - 1;
+        o.r[2] = c + 1;
+        o.wall[0] = false;
+        o.wall[2] = false;
+    }
+    return o;
+}
+
+__device__ __forceinline__ long long row_offset(const VDom &d, int y, int z) {
+    return ((long long)z * d.ny + y) * d.pitch + VANS_OFF;
+}
+
+// ----------------------------------------------------------- the drag ----
+// alpha = eps^2 nu / K and beta = eps^3 F_eps / sqrt(K) (drag law) with K and
+// F_eps per k_mode; ca, cb are the host-side constants of vans_internal.h.
+// inv_e = 1/eps.  Also returns d alpha/d eps and d beta/d eps when asked.
+template <bool DERIV>
+__device__ __forceinline__ void drag(const VDom &d, float e, float inv_e, float &alpha, float &beta,
+                                     float *dalpha = nullptr, float *dbeta = nullptr) {
+    float a = 0.f, b = 0.f, da = 0.f, db = 0.f;
+    if (d.k_mode == 0) {          // Ergun: 150 nu (1-eps)^2/(eps d_p^2), 1.75 (1-eps)/d_p
+        const float om = 1.f - e;
+        a = d.ca * om * om * inv_e;
+        b = d.cb * om;
+        if (DERIV) {
+            da = -d.ca * om * (1.f + e) * inv_e * inv_e;
+            db = -d.cb;
+        }
+    } else if (d.k_mode == 1) {   // fixed K, F_eps
+        a = d.ca * e * e;
+        b = d.cb * e * e * e;
+        if (DERIV) {
+            da = 2.f * d.ca * e;
+            db = 3.f * d.cb * e * e;
+        }
+    } else {                      // fixed K, F_eps(eps) = 1.75/sqrt(150 eps^3)
+        const float se = sqrtf(e);
+        a = d.ca * e * e;
+        b = d.cb * e * se;
+        if (DERIV) {
+            da = 2.f * d.ca * e;
+            db = 1.5f * d.cb * se;
+        }
+    }
+    if (d.drag_mode == 0) { a = b = da = db = 0.f; }
+    if (d.drag_mode == 1) { b = db = 0.f; }
+    alpha = a;
+    beta = b;
+    if (DERIV) { *dalpha = da; *dbeta = db; }
+}
+
+// ----------------------------------------------------- cell macroscopics ----
+// Moments of one cell (Eqs. 0moment and 1moment) from its pulled deviations
+// h_i = f_i - w_i eps(x) and the porosities eps~_i = eps(x + e_i).
+template <int Q>
+struct Macro {
+    float dl;            // sum_i h_i = eps rho - eps
+    float e0;            // eps(x)
+    float R, inv_e, rho; // eps rho, 1/eps, rho
+    float ge[3];         // grad eps (lattice stencil)
+    float j[3];          // sum_i e_i f_i
+    float Pc[3];         // p grad eps = cs^2 rho grad eps
+    float m[3];          // j + Pc/2 + R g/2
+    float alpha, beta;
+    float a, b, mm, sq, D, s; // velocity solve: D = a + sq, s = 2/D
+    float u[3], un;
+    float V[3];          // p grad eps + F, the vector P_i + F_i act on
+};
+
+template <int Q>
+__device__ __forceinline__ void macro(const VDom &d, const float h[Q], float e0, const float et[Q],
+                                      Macro<Q> &M) {
+    using L = Lat<Q>;
+    constexpr int D = L::D;
+    // Eq. 0moment: eps rho = sum f_i = eps(x) + sum h_i
+    float dl = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) dl += h[i];
+    M.dl = dl;
+    M.e0 = e0;
+    M.R = e0 + dl;
+    M.inv_e = __frcp_rn(e0);
+    M.rho = M.R * M.inv_e;
+    // grad eps = (1/cs^2) sum_i w_i e_i eps~_i, and sum_i e_i f_i = sum_i e_i h_i
+#pragma unroll
+    for (int c = 0; c < D; ++c) { M.ge[c] = 0.f; M.j[c] = 0.f; }
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        const float we = 3.f * L::w(i) * et[i];
+        if (L::ex(i)) { M.ge[0] += L::ex(i) * we; M.j[0] += L::ex(i) * h[i]; }
+        if (L::ey(i)) { M.ge[1] += L::ey(i) * we; M.j[1] += L::ey(i) * h[i]; }
+        if (D == 3 && L::ez(i)) { M.ge[2] += L::ez(i) * we; M.j[2] += L::ez(i) * h[i]; }
+    }
+    drag<false>(d, e0, M.inv_e, M.alpha, M.beta);
+    const float pc = M.rho * (1.f / 3.f);
+    float mm2 = 0.f;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        M.Pc[c] = pc * M.ge[c];
+        M.m[c] = M.j[c] + 0.5f * (M.Pc[c] + M.R * d.g[c]);
+        mm2 += M.m[c] * M.m[c];
+    }
+    // Eq. 1moment with the drag: (R + alpha/2 + beta/2 |u|) u = m, solved exactly
+    M.a = M.R + 0.5f * M.alpha;
+    M.b = 0.5f * M.beta;
+    M.mm = sqrtf(mm2);
+    M.sq = sqrtf(M.a * M.a + 4.f * M.b * M.mm);
+    M.D = M.a + M.sq;
+    M.s = __fdiv_rn(2.f, M.D);
+    M.un = M.mm * M.s;
+    const float kd = M.alpha + M.beta * M.un;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        M.u[c] = M.m[c] * M.s;
+        M.V[c] = M.Pc[c] + M.R * d.g[c] - kd * M.u[c];
+    }
+}
+
+// ---------------------------------------------------------- collision ----
+// f*_i = f_i - (f_i - f^eq_i)/tau + P_i + F_i (the final LBE), in deviation
+// form: with A_i = f^eq_i/w_i - eps(x) = dl + R (3 e.u + 4.5 (e.u)^2 - 1.5 u.u)
+// (Eq. d2q9eq) and S_i/w_i = (1 - 1/(2tau)) (3 (e_i - u) + 9 (e_i.u) e_i).V
+// (Eqs. pi and Fi), the stored value is
+//   o_i = (1 - omega) h_i + w_i [omega A_i + S_i/w_i + eps(x) - eps~_i].
+// Directions come in opposite pairs +c/-c, which share the even part of A and
+// S and flip the sign of the odd part.
+template <int Q>
+__device__ __forceinline__ void collide(const VDom &d, const float h[Q], float e0, const float et[Q],
+                                        float o[Q]) {
+    using L = Lat<Q>;
+    constexpr int D = L::D;
+    Macro<Q> M;
+    macro<Q>(d, h, e0, et, M);
+    const float om = d.omega, ct = d.ctau, om1 = 1.f - om;
+    float uu = 0.f, uV = 0.f;
+#pragma unroll
+    for (int c = 0; c < D; ++c) { uu += M.u[c] * M.u[c]; uV += M.u[c] * M.V[c]; }
+    const float symc = om * (M.dl - 1.5f * M.R * uu) - 3.f * ct * uV;
+    const float omR = om * M.R;
+    o[0] = om1 * h[0] + L::w(0) * symc;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        if (L::opp(i) < i) continue;               // handle each pair once, from its first member
+        const int j = L::opp(i);
+        float eu = 0.f, eV = 0.f;
+        if (L::ex(i)) { eu += L::ex(i) * M.u[0]; eV += L::ex(i) * M.V[0]; }
+        if (L::ey(i)) { eu += L::ey(i) * M.u[1]; eV += L::ey(i) * M.V[1]; }
+        if (D == 3 && L::ez(i)) { eu += L::ez(i) * M.u[2]; eV += L::ez(i) * M.V[2]; }
+        const float sym = symc + 4.5f * omR * eu * eu + 9.f * ct * eu * eV + e0;
+        const float anti = 3.f * (omR * eu + ct * eV);
+        o[i] = om1 * h[i] + L::w(i) * (sym + anti - et[i]);
+        o[j] = om1 * h[j] + L::w(j) * (sym - anti - et[j]);
+    }
+}
+
+}  // namespace vans

@@ -1,0 +1,68 @@
+// vans_internal.h -- types shared by the host runtime and the kernels (not part
+// of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define VANS_OFF 4  // column 0 of a padded row sits 4 floats (16 bytes) into the row
+
+namespace vans {
+
+// Everything a kernel needs to know about one domain.  Plain data, passed by
+// value to the single-domain kernels and stored in a device table for the
+// batched kernel.
+struct VDom {
+    int q, nx, ny, nz;
+    int rows;             // ny * nz padded rows per direction plane
+    int pitch;            // floats per padded row (multiple of 32)
+    long long plane;      // rows * pitch floats per direction
+    int wall_y, wall_z;   // 1: bounce-back walls on both faces of that axis
+    float omega;          // 1 / tau
+    float ctau;           // 1 - 1/(2 tau), the prefactor of Eqs. pi and Fi
+    float g[3];           // body force per unit mass
+    int drag_mode, k_mode;
+    float ca, cb;         // drag constants: alpha = ca * a(eps), beta = cb * b(eps)
+    const float *eps;     // padded porosity rows (same row layout, one plane)
+    float *f[2];          // the two state buffers (batched kernel only)
+    long long cells;      // nx * ny * nz
+    long long dense_off;  // offset of this domain in packed dense outputs (batched)
+};
+
+// One tile of the batched kernel: a block-sized piece of one domain.
+struct Tile {
+    int dom;   // domain index
+    int row;   // first row of the tile
+    int x0;    // first column of the tile
+    int pad;
+};
+
+struct Launch {
+    int cpt, warps, rows;
+};
+
+// ------------------------------------------------------ kernel launchers ----
+// Each returns cudaSuccess or the launch error.  `stream` is where they enqueue.
+
+cudaError_t launch_step(int q, const VDom &d, const float *fin, float *fout, Launch L,
+                        cudaStream_t stream);
+cudaError_t launch_step_batched(const VDom *doms_dev, const Tile *tiles_dev, int ntiles, int parity,
+                                Launch L, int grid, cudaStream_t stream);
+int batched_blocks_per_sm(Launch L);
+cudaError_t launch_moments(int q, const VDom &d, const float *state, float *rho, float *u,
+                           cudaStream_t stream);
+cudaError_t launch_export(int q, const VDom &d, const float *state, float *f, cudaStream_t stream);
+cudaError_t launch_import(int q, const VDom &d, const float *f, float *state, cudaStream_t stream);
+cudaError_t launch_pad_eps(const VDom &d, const float *eps_dense, float *eps_pad, int *flag,
+                           cudaStream_t stream);
+cudaError_t launch_check(int q, const VDom &d, const float *state, int *flag, cudaStream_t stream);
+cudaError_t launch_flux(int q, const VDom &d, const float *state, int x_out, float *J,
+                        cudaStream_t stream);
+cudaError_t launch_flux_seed(int q, const VDom &d, const float *state, int x_out, float *lam,
+                             float *grad, cudaStream_t stream);
+cudaError_t launch_step_adjoint(int q, const VDom &d, const float *state, const float *lam_in,
+                                float *lam_out, float *grad, cudaStream_t stream);
+cudaError_t launch_grad_finalize(int q, const VDom &d, const float *lam0, const float *grad,
+                                 float *dJ, cudaStream_t stream);
+
+}  // namespace vans

@@ -1,0 +1,201 @@
+// vans_step.cu -- the fused collide-and-stream step (the hot path).
+//
+// One kernel does the whole update of the final LBE with P_i and F_i for every
+// cell it owns: pull the Q populations from the previous step's buffer (periodic
+// wrap through the halo columns, half-way bounce-back at walls), form eps*rho and
+// the implicit velocity of Eq. 1moment (drag solved in closed form), build
+// f^eq (Eq. d2q9eq), P_i (Eq. pi) and F_i (Eq. Fi), relax and store.  Each
+// population is read once from HBM and written once; eps comes through L1/L2.
+//
+// Thread mapping: a warp covers 32*CPT consecutive cells of one row (y for
+// D2Q9, a (y,z) line for D3Q19); each lane owns CPT cells and loads them with
+// one aligned vector load per direction.  The +-1 column shift of the pull is
+// done with a warp shuffle, so every global load is an aligned vector load.
+#include "vans_device.cuh"
+
+namespace vans {
+
+template <int Q, int CPT, bool EDGE>
+__device__ __forceinline__ void step_row(const VDom &d, const float *__restrict__ fin,
+                                         float *__restrict__ fout, int y, int z, int x0, int lane) {
+    using L = Lat<Q>;
+    const Nb3 Y = nb3<EDGE>(y, d.ny, d.wall_y);
+    Nb3 Z;
+    if (Q == 19) {
+        Z = nb3<EDGE>(z, d.nz, d.wall_z);
+    } else {
+        Z.r[0] = Z.r[1] = Z.r[2] = 0;
+        Z.wall[0] = Z.wall[1] = Z.wall[2] = false;
+    }
+
+    // S1: pull.  h_i(x) = stored deviation at x - e_i, or the opposite
+    // direction of x itself when x - e_i lies past a wall.
+    float h[Q][CPT];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
+        const bool bb = Y.wall[1 - ey] || Z.wall[1 - ez];
+        const int si = bb ? L::opp(i) : i;
+        const long long ro = bb ? row_offset(d, y, z) : row_offset(d, Y.r[1 - ey], Z.r[1 - ez]);
+        ld_shift<CPT>(fin + si * d.plane + ro, x0, bb ? 0 : -ex, lane, h[i]);
+    }
+
+    // porosity of the cell and of its Q-1 neighbours (for grad eps and the
+    // deviation shift), from the padded eps rows
+    float E[3][3][CPT + 2];
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz) {
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy) {
+            if (Q == 9 && dz != 0) continue;
+            const float *row = d.eps + row_offset(d, Y.r[1 + dy], Z.r[1 + dz]);
+            if (dy != 0 && dz != 0) {
+                float t[CPT];
+                ld_vec<CPT>(row + x0, t);
+#pragma unroll
+                for (int k = 0; k < CPT; ++k) E[1 + dy][1 + dz][k + 1] = t[k];
+            } else {
+                ld_ext<CPT>(row, x0, lane, E[1 + dy][1 + dz]);
+            }
+        }
+    }
+
+    float out[Q][CPT];
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) {
+        float hh[Q], et[Q];
+        const float e0 = E[1][1][k + 1];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            hh[i] = h[i][k];
+            const bool wall = Y.wall[1 + L::ey(i)] || Z.wall[1 + L::ez(i)];
+            et[i] = (i == 0 || wall) ? e0 : E[1 + L::ey(i)][1 + L::ez(i)][k + 1 + L::ex(i)];
+        }
+        float o[Q];
+        collide<Q>(d, hh, e0, et, o);   // S2-S7
+#pragma unroll
+        for (int i = 0; i < Q; ++i) out[i][k] = o[i];
+    }
+
+    const long long ro = row_offset(d, y, z);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) st_masked<CPT>(fout + i * d.plane + ro, x0, d.nx, out[i]);
+    // halo copies: column nx mirrors column 0 for directions moving -x, column
+    // -1 mirrors column nx-1 for directions moving +x
+    if (x0 == 0) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+            if (L::ex(i) < 0) fout[i * d.plane + ro + d.nx] = out[i][0];
+    }
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) {
+        if (x0 + k == d.nx - 1) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i)
+                if (L::ex(i) > 0) fout[i * d.plane + ro - 1] = out[i][k];
+        }
+    }
+}
+
+template <int Q, int CPT>
+__global__ void __launch_bounds__(256) k_step(const VDom d, const float *__restrict__ fin,
+                                              float *__restrict__ fout, int nxb) {
+    const int lane = threadIdx.x & 31;
+    const int wx = threadIdx.x >> 5;
+    const int bx = blockIdx.x % nxb;
+    const int by = blockIdx.x / nxb;
+    const int r = by * blockDim.y + threadIdx.y;
+    if (r >= d.rows) return;                               // whole warp
+    const int xw = (bx * (blockDim.x >> 5) + wx) * 32 * CPT;
+    if (xw >= d.nx) return;                                // whole warp
+    const int x0 = xw + lane * CPT;
+    const int y = r % d.ny, z = r / d.ny;
+    const bool edge = (y == 0) || (y == d.ny - 1) || (Q == 19 && (z == 0 || z == d.nz - 1));
+    if (edge)
+        step_row<Q, CPT, true>(d, fin, fout, y, z, x0, lane);
+    else
+        step_row<Q, CPT, false>(d, fin, fout, y, z, x0, lane);
+}
+
+// Batched D2Q9: one persistent grid walks a flattened list of equal-shaped
+// tiles drawn from all domains; each tile carries its domain index, whose
+// descriptor (sizes, tau, drag constants, buffers) comes from a device table.
+template <int CPT>
+__global__ void __launch_bounds__(256) k_step_batched(const VDom *__restrict__ doms,
+                                                      const Tile *__restrict__ tiles, int ntiles,
+                                                      int parity) {
+    const int lane = threadIdx.x & 31;
+    const int wx = threadIdx.x >> 5;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const Tile T = tiles[t];
+        const VDom d = doms[T.dom];
+        const int r = T.row + threadIdx.y;
+        const int xw = T.x0 + wx * 32 * CPT;
+        if (r < d.rows && xw < d.nx) {                     // whole warp
+            const int x0 = xw + lane * CPT;
+            const float *fin = parity ? d.f[1] : d.f[0];
+            float *fout = parity ? d.f[0] : d.f[1];
+            if (r == 0 || r == d.ny - 1)
+                step_row<9, CPT, true>(d, fin, fout, r, 0, x0, lane);
+            else
+                step_row<9, CPT, false>(d, fin, fout, r, 0, x0, lane);
+        }
+    }
+}
+
+template <int Q, int CPT>
+static cudaError_t launch_step_t(const VDom &d, const float *fin, float *fout, Launch L,
+                                 cudaStream_t stream) {
+    const int cells_per_block_x = 32 * CPT * L.warps;
+    const int nxb = (d.nx + cells_per_block_x - 1) / cells_per_block_x;
+    const int nrb = (d.rows + L.rows - 1) / L.rows;
+    const long long nblocks = (long long)nxb * nrb;
+    if (nblocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    dim3 block(32 * L.warps, L.rows);
+    k_step<Q, CPT><<<(unsigned)nblocks, block, 0, stream>>>(d, fin, fout, nxb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step(int q, const VDom &d, const float *fin, float *fout, Launch L,
+                        cudaStream_t stream) {
+    if (q == 9) {
+        switch (L.cpt) {
+            case 1: return launch_step_t<9, 1>(d, fin, fout, L, stream);
+            case 2: return launch_step_t<9, 2>(d, fin, fout, L, stream);
+            case 4: return launch_step_t<9, 4>(d, fin, fout, L, stream);
+        }
+    } else if (q == 19) {
+        switch (L.cpt) {
+            case 1: return launch_step_t<19, 1>(d, fin, fout, L, stream);
+            case 2: return launch_step_t<19, 2>(d, fin, fout, L, stream);
+            case 4: return launch_step_t<19, 4>(d, fin, fout, L, stream);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+int batched_blocks_per_sm(Launch L) {
+    int n = 0;
+    const int threads = 32 * L.warps * L.rows;
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (L.cpt) {
+        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_batched<1>, threads, 0); break;
+        case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_batched<2>, threads, 0); break;
+        case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_batched<4>, threads, 0); break;
+    }
+    return (e == cudaSuccess && n > 0) ? n : 1;
+}
+
+cudaError_t launch_step_batched(const VDom *doms_dev, const Tile *tiles_dev, int ntiles, int parity,
+                                Launch L, int grid, cudaStream_t stream) {
+    dim3 block(32 * L.warps, L.rows);
+    switch (L.cpt) {
+        case 1: k_step_batched<1><<<grid, block, 0, stream>>>(doms_dev, tiles_dev, ntiles, parity); break;
+        case 2: k_step_batched<2><<<grid, block, 0, stream>>>(doms_dev, tiles_dev, ntiles, parity); break;
+        case 4: k_step_batched<4><<<grid, block, 0, stream>>>(doms_dev, tiles_dev, ntiles, parity); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace vans

@@ -1,0 +1,206 @@
+"""GPU parity of the fused step, the moments and the state I/O against the FP64
+oracle, on seeded inputs, through the C ABI (libvans.so)."""
+import numpy as np
+import pytest
+
+from paper_1406_6438_gb300 import workloads as W
+from paper_1406_6438_gb300._binding import Launch, VansError
+from tests._gpu import gpu_run, oracle_run, rel_u, solver, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def _case(q, shape, wall_mask, seed, tau=0.7, k_mode=0):
+    nz, ny, nx = shape
+    p = W.params(q=q, nx=nx, ny=ny, nz=nz, wall_mask=wall_mask, tau=tau,
+                 g=(3e-4, -1e-4, 5e-5), drag_mode=2, k_mode=k_mode, d_p=6.0, K=2.5, F_eps=0.3)
+    eps = W.smoothed_noise(shape, 2.0, 0.4, 1.0, seed)
+    f0 = W.random_state(q, eps, seed + 100, amp=0.02)
+    return p, eps, f0
+
+
+STEP_CASES = [
+    # q, (nz, ny, nx), wall_mask, launches
+    (9, (1, 13, 37), 2, [Launch(1, 1, 2), Launch(2, 2, 1), Launch(4, 1, 2), Launch(4, 4, 1)]),
+    (9, (1, 6, 5), 0, [Launch(4, 2, 1), Launch(1, 2, 1)]),
+    (9, (1, 1, 1), 0, [Launch(4, 2, 1)]),
+    (9, (1, 1, 3), 2, [Launch(1, 2, 1)]),
+    (9, (1, 9, 300), 2, [Launch(2, 2, 2), Launch(4, 2, 1)]),
+    (19, (7, 9, 21), 6, [Launch(1, 2, 1), Launch(2, 2, 2), Launch(4, 1, 2)]),
+    (19, (5, 4, 33), 2, [Launch(2, 2, 1)]),
+    (19, (3, 3, 4), 0, [Launch(1, 2, 1)]),
+    (19, (1, 1, 2), 6, [Launch(1, 2, 1)]),
+]
+
+
+@pytest.mark.parametrize("q,shape,wm,launches", STEP_CASES)
+@pytest.mark.parametrize("nsteps", [1, 7])
+def test_step_matches_oracle_on_random_states(q, shape, wm, launches, nsteps):
+    """Every population after 1 and 7 steps from a random near-rest state, for
+    several launch shapes (cells per thread, warps, rows), ragged nx, tiny
+    grids, periodic and bounce-back axes.  Tolerance: a few FP32 ulps of f."""
+    p, eps, f0 = _case(q, shape, wm, seed=sum(shape) + wm)
+    rho_o, u_o, f_o = oracle_run(p, eps, nsteps, f0)
+    for L in launches:
+        rho, u, f = gpu_run(p, eps, nsteps, f0, launch=L)
+        assert np.abs(f - f_o).max() <= 2e-7, (L, np.abs(f - f_o).max())
+        assert np.abs(rho - rho_o).max() <= 1e-6, L
+        assert rel_u(u, u_o) <= 1e-5, (L, rel_u(u, u_o))
+
+
+@pytest.mark.parametrize("k_mode", [0, 1, 2])
+def test_drag_modes(k_mode):
+    p, eps, f0 = _case(9, (1, 12, 20), 2, seed=5 + k_mode, k_mode=k_mode)
+    for dm in (0, 1, 2):
+        p["drag_mode"] = dm
+        rho_o, u_o, f_o = oracle_run(p, eps, 20, f0)
+        rho, u, f = gpu_run(p, eps, 20, f0)
+        assert np.abs(f - f_o).max() <= 2e-7
+        assert rel_u(u, u_o) <= 1e-5
+
+
+def test_channel_128x64_5000_steps():
+    """The 128x64 porous Poiseuille channel (uniform eps = 0.6, Da = 1e-3,
+    Forchheimer on, tau = 0.8) after 5000 steps from rest: FP32 GPU velocity
+    within 1e-5 of the FP64 oracle, relative to max|u|."""
+    p, eps, n = W.channel_128x64()
+    rho_o, u_o, _ = oracle_run(p, eps, n)
+    rho, u, _ = gpu_run(p, eps, n)
+    assert rel_u(u, u_o) <= 1e-5, rel_u(u, u_o)
+    assert np.abs(rho - rho_o).max() <= 1e-5
+
+
+def test_periodic_noise_field_downsized():
+    """The periodic smoothed-noise workload (eps in [0.4, 1], tau = 0.6, Ergun
+    drag, body force) on a 96x80 grid for 200 steps."""
+    p, eps, n = W.periodic_2d_shape(96, 80, nsteps=200)
+    rho_o, u_o, _ = oracle_run(p, eps, n)
+    rho, u, _ = gpu_run(p, eps, n)
+    assert rel_u(u, u_o) <= 1e-5, rel_u(u, u_o)
+    assert np.abs(rho - rho_o).max() <= 1e-5
+
+
+def test_d3q19_duct_downsized():
+    """The D3Q19 porous duct (walls on y and z, eps in [0.35, 0.95]) on a
+    40x24x20 grid for 100 steps."""
+    p, eps, n = W.duct_3d(nx=40, ny=24, nz=20, nsteps=100)
+    rho_o, u_o, _ = oracle_run(p, eps, n)
+    rho, u, _ = gpu_run(p, eps, n)
+    assert rel_u(u, u_o) <= 1e-5, rel_u(u, u_o)
+    assert np.abs(rho - rho_o).max() <= 1e-5
+
+
+def test_graph_replay_equals_single_launches():
+    """vans_step(n) replays a captured CUDA graph for long runs; the result is
+    bit-identical to n single steps."""
+    torch = torch_cuda()
+    p, eps, n = W.periodic_2d_shape(70, 50, nsteps=0)
+    a = solver(p, eps)
+    b = solver(p, eps)
+    a.step(64 * 2 + 3)
+    for _ in range(64 * 2 + 3):
+        b.step(1)
+    fa, fb = a.get_state(), b.get_state()
+    torch.cuda.synchronize()
+    assert torch.equal(fa, fb)
+    # and an odd start parity before the graph
+    a.step(1)
+    a.step(65)
+    for _ in range(66):
+        b.step(1)
+    assert torch.equal(a.get_state(), b.get_state())
+
+
+def test_checkpoint_resume_is_bitwise():
+    """Stop, save the state, continue; restore, continue again: identical."""
+    torch = torch_cuda()
+    p, eps, _ = W.periodic_2d_shape(64, 40, nsteps=0)
+    s = solver(p, eps)
+    s.step(30)
+    ck = s.get_state()
+    s.step(77)
+    ref = s.get_state().clone()
+    s.set_state(ck)
+    s.step(77)
+    torch.cuda.synchronize()
+    assert torch.equal(s.get_state(), ref)
+
+
+def test_autotune_leaves_state_unchanged():
+    torch = torch_cuda()
+    p, eps, _ = W.periodic_2d_shape(200, 64, nsteps=0)
+    a = solver(p, eps)
+    b = solver(p, eps)
+    a.step(10)
+    b.step(10)
+    L = a.autotune()
+    assert L.cpt in (1, 2, 4)
+    b.launch = L
+    a.step(10)
+    b.step(10)
+    torch.cuda.synchronize()
+    assert torch.equal(a.get_state(), b.get_state())
+
+
+def test_populations_roundtrip():
+    torch = torch_cuda()
+    p, eps, f0 = _case(9, (1, 10, 23), 2, seed=3)
+    s = solver(p, eps)
+    ft = torch.from_numpy(f0).cuda()
+    s.set_populations(ft)
+    back = s.populations()
+    torch.cuda.synchronize()
+    assert (back - ft).abs().max().item() <= 6e-8
+
+
+def test_launch_shapes_agree_on_a_long_run():
+    p, eps, n = W.periodic_2d_shape(150, 40, nsteps=300)
+    ref = None
+    for L in (Launch(1, 2, 1), Launch(2, 4, 2), Launch(4, 4, 1), Launch(4, 2, 4)):
+        rho, u, f = gpu_run(p, eps, n, launch=L)
+        if ref is None:
+            ref = u
+        else:
+            assert rel_u(u, ref) <= 1e-6
+
+
+@pytest.mark.parametrize("wm", [0, 2])
+def test_mass_conserved_on_gpu(wm):
+    """Total mass over 2000 steps drifts by FP32 rounding only."""
+    torch = torch_cuda()
+    p, eps, _ = W.periodic_2d_shape(128, 96, nsteps=0)
+    p["wall_mask"] = wm
+    s = solver(p, eps)
+    m0 = s.populations().double().sum().item()
+    s.step(2000)
+    m1 = s.populations().double().sum().item()
+    assert abs(m1 - m0) <= 1e-6 * m0
+
+
+def test_errors_reported():
+    torch = torch_cuda()
+    import paper_1406_6438_gb300 as V
+    p, eps, _ = W.periodic_2d_shape(16, 8, nsteps=0)
+    s = V.Solver(p)
+    with pytest.raises(VansError) as e:
+        s.step(1)
+    assert e.value.status == -6
+    bad = torch.from_numpy(eps.copy()).cuda().view(-1)
+    bad[5] = 0.0
+    with pytest.raises(VansError) as e:
+        s.set_eps(bad)
+    assert e.value.status == -1
+    bad[5] = float("nan")
+    with pytest.raises(VansError):
+        s.set_eps(bad)
+    bad[5] = 1.5
+    with pytest.raises(VansError):
+        s.set_eps(bad)
+    s.set_eps(torch.from_numpy(eps).cuda().view(-1))
+    with pytest.raises(VansError):
+        s.step(-1)
+    assert s.check()
+    f = s.populations()
+    f[3, 0, 2, 2] = float("nan")          # a fault injected on the host side
+    s.set_populations(f)
+    assert not s.check()
