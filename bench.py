@@ -285,6 +285,8 @@ def main():
     ap.add_argument("--n", type=int, default=4096, help="domain edge (default 4096)")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--launch", default=None,
+                    help="fixed launch shape cpt,warps,rows instead of the autotuner")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -307,7 +309,12 @@ def main():
     cells = p["nx"] * p["ny"]
     sim = V.Solver(p)
     sim.set_eps(torch.from_numpy(eps).cuda().view(-1))
-    L = sim.autotune()
+    if args.launch:
+        cpt, warps, rows = (int(v) for v in args.launch.split(","))
+        sim.launch = V.Launch(cpt, warps, rows)
+        L = sim.launch
+    else:
+        L = sim.autotune()
     sim.step(args.warmup)
     if dist:
         dist.barrier()

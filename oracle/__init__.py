@@ -20,6 +20,10 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
+# OpenMP threads sleep instead of spinning when idle, so the oracle degrades
+# gracefully when the host cores are shared (set before the runtime loads)
+os.environ.setdefault("OMP_WAIT_POLICY", "PASSIVE")
+
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "vans_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")

@@ -292,8 +292,8 @@ __device__ __forceinline__ void collide_vjp(const VDom &d, const float h[Q], flo
 
 // J = sum over the plane x = x_out of eps rho u_x; one block, fixed-order sum.
 template <int Q>
-__global__ void k_flux(const VDom d, const float *__restrict__ st, int x_out, float *J) {
-    __shared__ float red[1024];
+__global__ void __launch_bounds__(256) k_flux(const VDom d, const float *__restrict__ st, int x_out, float *J) {
+    __shared__ float red[256];
     float acc = 0.f;
     for (int r = threadIdx.x; r < d.rows; r += blockDim.x) {
         const int y = r % d.ny, z = r / d.ny;
@@ -558,8 +558,8 @@ cudaError_t launch_check(int q, const VDom &d, const float *state, int *flag, cu
 
 cudaError_t launch_flux(int q, const VDom &d, const float *state, int x_out, float *J,
                         cudaStream_t s) {
-    VANS_DISPATCH_Q(q, (k_flux<9><<<1, 1024, 0, s>>>(d, state, x_out, J)),
-                    (k_flux<19><<<1, 1024, 0, s>>>(d, state, x_out, J)));
+    VANS_DISPATCH_Q(q, (k_flux<9><<<1, 256, 0, s>>>(d, state, x_out, J)),
+                    (k_flux<19><<<1, 256, 0, s>>>(d, state, x_out, J)));
     return cudaGetLastError();
 }
 
