@@ -188,6 +188,29 @@ int vans_batch_autotune(vans_t h, vans_launch *chosen);
 /* Cells summed over all domains. */
 long long vans_batch_cells(vans_t h);
 
+/* ------------------------------------------------- no-allocation step --- */
+
+/* One step from state_in to state_out (vans_state_floats(p) floats each,
+ * distinct buffers; an all-zero buffer is the rest state f = w eps) for a
+ * caller that cannot allocate device memory or hand the library a workspace:
+ * code that runs inside another framework's memory pool or allocator, code that
+ * may not call cudaMalloc while a CUDA graph is being captured, or an embedded
+ * host whose device memory budget is fixed in advance.  It needs no handle and
+ * allocates nothing: the only scratch the step uses besides the caller's
+ * buffers, the padded copy of eps (dense nx*ny*nz floats, 0 < eps <= 1; not
+ * range-checked here), is a 16 MiB array that the library holds in device
+ * memory on every GPU where it is loaded, until the process exits.
+ * Limit: ny*nz rows times the padded row length (nx rounded up to 128, plus 5,
+ * rounded up to 32 floats) must not exceed 4 Mi floats, e.g. up to about a
+ * 2000 x 2000 D2Q9 or a 150^3 D3Q19 domain; larger domains get VANS_ERR_ARG.
+ * Parameter errors as in vans_create.  The first call on a device looks up the
+ * array's device address; make that first call before any stream capture.
+ * All calls share the array, so calls whose GPU work overlaps (on different
+ * streams or threads) race and must be serialised by the caller.  The paper has
+ * no counterpart to this entry point. */
+int vans_step_static(const vans_params *p, const float *eps_dev, const float *state_in,
+                     float *state_out, void *cuda_stream);
+
 /* ---------------------------------------------------------------- misc --- */
 
 /* Total cells of the handle (single domain: nx*ny*nz). */
