@@ -286,7 +286,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--launch", default=None,
-                    help="fixed launch shape cpt,warps,rows instead of the autotuner")
+                    help="fixed launch shape cpt,warps,rows[,kind] instead of the autotuner")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -310,8 +310,7 @@ def main():
     sim = V.Solver(p)
     sim.set_eps(torch.from_numpy(eps).cuda().view(-1))
     if args.launch:
-        cpt, warps, rows = (int(v) for v in args.launch.split(","))
-        sim.launch = V.Launch(cpt, warps, rows)
+        sim.launch = V.Launch(*(int(v) for v in args.launch.split(",")))
         L = sim.launch
     else:
         L = sim.autotune()

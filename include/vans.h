@@ -74,11 +74,21 @@ typedef struct {
     float F_eps;    /* geometric function (k_mode 1)                                 */
 } vans_params;
 
-/* Launch configuration of the step kernels (chosen by vans_autotune). */
+/* Launch configuration of the step kernels (chosen by vans_autotune).
+ * kind 0: register-load kernel: cpt cells per lane (1, 2, 4), `warps` warps
+ *         along x times `rows` rows per block (warps*rows <= 8).
+ * kind 1: bulk-copy pipeline kernel (persistent CTAs, rows staged in shared
+ *         memory by cp.async.bulk): 32*warps threads (warps 4 or 8), cpt cells
+ *         per thread per tile (1, 2, 4), `rows` = pipeline stages (2..6).
+ * kind 2: D2Q9 only: the kind-1 pipeline where each CTA walks a vertical strip
+ *         of tiles and keeps the porosity rows in a shared-memory ring, so each
+ *         eps row is read from HBM once per strip.
+ *         Kinds 1 and 2 are not available to the batched path. */
 typedef struct {
-    int cpt;        /* cells per thread along x: 1, 2 or 4                           */
-    int warps;      /* warps per block along x: 1..8                                 */
-    int rows;       /* rows (y, or y*z lines) per block: 1..8                        */
+    int cpt;
+    int warps;
+    int rows;
+    int kind;
 } vans_launch;
 
 /* ---------------------------------------------------------------- sizes -- */

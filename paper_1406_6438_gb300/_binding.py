@@ -37,7 +37,8 @@ class _CParams(ctypes.Structure):
 
 
 class _CLaunch(ctypes.Structure):
-    _fields_ = [("cpt", ctypes.c_int), ("warps", ctypes.c_int), ("rows", ctypes.c_int)]
+    _fields_ = [("cpt", ctypes.c_int), ("warps", ctypes.c_int), ("rows", ctypes.c_int),
+                ("kind", ctypes.c_int)]
 
 
 @dataclass
@@ -84,9 +85,13 @@ class Params:
 
 @dataclass
 class Launch:
+    """kind 0: register-load kernel (cpt cells per lane, warps x rows per block);
+    kind 1: bulk-copy pipeline (32*warps threads, cpt cells per thread per tile,
+    rows = pipeline stages)."""
     cpt: int
     warps: int
     rows: int
+    kind: int = 0
 
 
 _lib = None
@@ -285,17 +290,17 @@ class Solver:
     def autotune(self) -> Launch:
         c = _CLaunch()
         _check(self.lib.vans_autotune(self._h, ctypes.byref(c)), "vans_autotune")
-        return Launch(c.cpt, c.warps, c.rows)
+        return Launch(c.cpt, c.warps, c.rows, c.kind)
 
     @property
     def launch(self) -> Launch:
         c = _CLaunch()
         _check(self.lib.vans_get_launch(self._h, ctypes.byref(c)), "vans_get_launch")
-        return Launch(c.cpt, c.warps, c.rows)
+        return Launch(c.cpt, c.warps, c.rows, c.kind)
 
     @launch.setter
     def launch(self, L: Launch):
-        c = _CLaunch(int(L.cpt), int(L.warps), int(L.rows))
+        c = _CLaunch(int(L.cpt), int(L.warps), int(L.rows), int(L.kind))
         _check(self.lib.vans_set_launch(self._h, ctypes.byref(c)), "vans_set_launch")
 
     @property
@@ -399,17 +404,17 @@ class Batch:
     def autotune(self) -> Launch:
         c = _CLaunch()
         _check(self.lib.vans_batch_autotune(self._h, ctypes.byref(c)), "vans_batch_autotune")
-        return Launch(c.cpt, c.warps, c.rows)
+        return Launch(c.cpt, c.warps, c.rows, c.kind)
 
     @property
     def launch(self) -> Launch:
         c = _CLaunch()
         _check(self.lib.vans_get_launch(self._h, ctypes.byref(c)), "vans_get_launch")
-        return Launch(c.cpt, c.warps, c.rows)
+        return Launch(c.cpt, c.warps, c.rows, c.kind)
 
     @launch.setter
     def launch(self, L: Launch):
-        c = _CLaunch(int(L.cpt), int(L.warps), int(L.rows))
+        c = _CLaunch(int(L.cpt), int(L.warps), int(L.rows), int(L.kind))
         _check(self.lib.vans_set_launch(self._h, ctypes.byref(c)), "vans_set_launch")
 
     @property

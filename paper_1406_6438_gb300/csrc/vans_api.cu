@@ -96,11 +96,22 @@ void fill_dom(const vans_params *p, VDom &d) {
     d.cells = (long long)p->nx * p->ny * p->nz;
 }
 
-bool launch_ok(const vans_launch *c) {
+bool launch_ok(const vans_launch *c, int q, bool batched) {
     if (!c) return false;
     if (c->cpt != 1 && c->cpt != 2 && c->cpt != 4) return false;
-    if (c->warps < 1 || c->warps > 8 || c->rows < 1 || c->rows > 8) return false;
-    return c->warps * c->rows <= 8;
+    if (c->kind == 0) {
+        if (c->warps < 1 || c->warps > 8 || c->rows < 1 || c->rows > 8) return false;
+        return c->warps * c->rows <= 8;
+    }
+    if ((c->kind != 1 && c->kind != 2) || batched) return false;
+    if (c->rows < 2 || c->rows > 6) return false;
+    // the instantiated pipeline shapes
+    const int nt = 32 * c->warps;
+    if (c->kind == 2)
+        return q == 9 && ((nt == 128 && (c->cpt == 2 || c->cpt == 4)) || (nt == 256 && c->cpt <= 2));
+    if (q == 9)
+        return (nt == 128 && (c->cpt == 2 || c->cpt == 4)) || (nt == 256 && c->cpt <= 2);
+    return (nt == 128 && c->cpt <= 2) || (nt == 256 && c->cpt == 1);
 }
 
 }  // namespace
@@ -112,7 +123,7 @@ struct vans_s {
     cudaStream_t cap = nullptr;                 // private stream for graph capture
     int device = 0;
     long long launches = 0;
-    Launch L{4, 4, 1};
+    Launch L{4, 4, 1, 0};
     cudaGraphExec_t gexec = nullptr;
     int *flag = nullptr;                        // device status words (workspace)
     // single domain
@@ -213,13 +224,15 @@ int make_streams(vans_t h, void *stream) {
     return VANS_OK;
 }
 
-// read and clear the status word; synchronises the stream
-int read_flag(vans_t h, int *value) {
-    int v = 0;
-    if (cudaMemcpyAsync(&v, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+// read the status words (flag[0]: range / divergence, flag[1]: a bounded
+// wait in a kernel timed out); synchronises the stream
+int read_flag(vans_t h, int *value, int *timeout = nullptr) {
+    int v[2] = {0, 0};
+    if (cudaMemcpyAsync(v, h->flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
         return VANS_ERR_CUDA;
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return VANS_ERR_CUDA;
-    *value = v;
+    *value = v[0];
+    if (timeout) *timeout = v[1];
     return VANS_OK;
 }
 
@@ -268,7 +281,7 @@ float time_launches(vans_t h, F &&fn, int reps) {
     return ms;
 }
 
-std::vector<Launch> candidates(int q) {
+std::vector<Launch> candidates(int q, bool batched) {
     std::vector<Launch> c;
     const int cpts[3] = {1, 2, 4};
     for (int cpt : cpts)
@@ -276,8 +289,21 @@ std::vector<Launch> candidates(int q) {
             for (int rows = 1; rows <= 4; rows *= 2) {
                 if (warps * rows > 8 || warps * rows < 2) continue;
                 if (q == 19 && cpt == 4 && warps * rows > 4) continue;
-                c.push_back(Launch{cpt, warps, rows});
+                c.push_back(Launch{cpt, warps, rows, 0});
             }
+    if (batched) return c;
+    // bulk-copy pipeline shapes {cpt, warps, stages, 1}
+    if (q == 9) {
+        const Launch t[] = {{2, 4, 3, 1}, {2, 4, 4, 1}, {4, 4, 2, 1}, {4, 4, 3, 1},
+                            {1, 8, 3, 1}, {1, 8, 4, 1}, {2, 8, 2, 1}, {2, 8, 3, 1},
+                            {2, 4, 3, 2}, {2, 4, 4, 2}, {4, 4, 3, 2}, {1, 8, 3, 2},
+                            {1, 8, 4, 2}, {2, 8, 3, 2}};
+        c.insert(c.end(), t, t + 14);
+    } else {
+        const Launch t[] = {{1, 4, 3, 1}, {1, 4, 4, 1}, {2, 4, 2, 1}, {2, 4, 3, 1},
+                            {1, 8, 2, 1}, {1, 8, 3, 1}};
+        c.insert(c.end(), t, t + 6);
+    }
     return c;
 }
 
@@ -318,7 +344,8 @@ int vans_create(const vans_params *p, void *workspace, size_t workspace_bytes, v
     h->eps_pad = w + 2 * h->sfloats;
     h->flag = (int *)(h->eps_pad + eps_floats_of(p->nx, p->ny, p->nz));
     h->dom.eps = h->eps_pad;
-    h->L = (p->q == 9) ? Launch{4, 4, 1} : Launch{2, 4, 1};
+    h->dom.status = h->flag + 1;
+    h->L = (p->q == 9) ? Launch{4, 4, 1, 0} : Launch{2, 4, 1, 0};
     int rc = make_streams(h, cuda_stream);
     if (rc) {
         vans_destroy(h);
@@ -414,12 +441,13 @@ int vans_get_launch(vans_t h, vans_launch *cfg) {
     cfg->cpt = h->L.cpt;
     cfg->warps = h->L.warps;
     cfg->rows = h->L.rows;
+    cfg->kind = h->L.kind;
     return VANS_OK;
 }
 
 int vans_set_launch(vans_t h, const vans_launch *cfg) {
-    if (!h || !launch_ok(cfg)) return VANS_ERR_ARG;
-    const Launch L{cfg->cpt, cfg->warps, cfg->rows};
+    if (!h || !launch_ok(cfg, h->q, h->batched)) return VANS_ERR_ARG;
+    const Launch L{cfg->cpt, cfg->warps, cfg->rows, cfg->kind};
     if (h->batched) return set_batch_launch(h, L);
     h->L = L;
     drop_graph(h);
@@ -431,7 +459,7 @@ int vans_autotune(vans_t h, vans_launch *chosen) {
     if (!h->eps_set) return VANS_ERR_STATE;
     // time each candidate on the current state; the output goes to the other
     // buffer, which holds nothing live, so the state is unchanged
-    const std::vector<Launch> cs = candidates(h->q);
+    const std::vector<Launch> cs = candidates(h->q, false);
     Launch best = h->L;
     float best_ms = 1e30f;
     const float *in = h->st[h->cur];
@@ -453,6 +481,7 @@ int vans_autotune(vans_t h, vans_launch *chosen) {
         chosen->cpt = best.cpt;
         chosen->warps = best.warps;
         chosen->rows = best.rows;
+        chosen->kind = best.kind;
     }
     return VANS_OK;
 }
@@ -515,9 +544,10 @@ int vans_check(vans_t h) {
         if (vans::launch_check(h->q, h->dom, h->st[h->cur], h->flag, h->stream) != cudaSuccess)
             return VANS_ERR_CUDA;
     }
-    int bad = 0;
-    int rc = read_flag(h, &bad);
+    int bad = 0, tmo = 0;
+    int rc = read_flag(h, &bad, &tmo);
     if (rc) return rc;
+    if (tmo) return VANS_ERR_TIMEOUT;
     return bad ? VANS_ERR_DIVERGED : VANS_OK;
 }
 
@@ -600,7 +630,7 @@ int vans_batch_create(const vans_params *p, int n, void *workspace, size_t works
         vans_destroy(h);
         return VANS_ERR_CUDA;
     }
-    rc = set_batch_launch(h, Launch{4, 4, 1});
+    rc = set_batch_launch(h, Launch{4, 4, 1, 0});
     if (rc) {
         vans_destroy(h);
         return rc;
@@ -661,7 +691,7 @@ int vans_batch_autotune(vans_t h, vans_launch *chosen) {
     Launch best = keep;
     float best_ms = 1e30f;
     const int par = h->parity;
-    for (const Launch &L : candidates(9)) {
+    for (const Launch &L : candidates(9, true)) {
         if (set_batch_launch(h, L) != VANS_OK) continue;
         // reads the current parity and writes the other buffer of every domain
         const float ms = time_launches(
@@ -684,6 +714,7 @@ int vans_batch_autotune(vans_t h, vans_launch *chosen) {
         chosen->cpt = best.cpt;
         chosen->warps = best.warps;
         chosen->rows = best.rows;
+        chosen->kind = best.kind;
     }
     return VANS_OK;
 }

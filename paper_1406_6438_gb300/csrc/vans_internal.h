@@ -27,6 +27,7 @@ struct VDom {
     float *f[2];          // the two state buffers (batched kernel only)
     long long cells;      // nx * ny * nz
     long long dense_off;  // offset of this domain in packed dense outputs (batched)
+    int *status;          // device status word: bit 1 = a bounded wait timed out
 };
 
 // One tile of the batched kernel: a block-sized piece of one domain.
@@ -37,8 +38,11 @@ struct Tile {
     int pad;
 };
 
+// kind 0: register-load kernel k_step (cpt cells per lane, warps x rows per block)
+// kind 1: bulk-copy pipeline k_step_tma (32*warps threads, cpt cells per thread
+//         per tile, rows = pipeline stages)
 struct Launch {
-    int cpt, warps, rows;
+    int cpt, warps, rows, kind;
 };
 
 // ------------------------------------------------------ kernel launchers ----
@@ -46,6 +50,8 @@ struct Launch {
 
 cudaError_t launch_step(int q, const VDom &d, const float *fin, float *fout, Launch L,
                         cudaStream_t stream);
+cudaError_t launch_step_tma(int q, const VDom &d, const float *fin, float *fout, Launch L,
+                            cudaStream_t stream);
 cudaError_t launch_step_batched(const VDom *doms_dev, const Tile *tiles_dev, int ntiles, int parity,
                                 Launch L, int grid, cudaStream_t stream);
 int batched_blocks_per_sm(Launch L);

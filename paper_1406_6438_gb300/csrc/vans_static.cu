@@ -90,7 +90,7 @@ extern "C" int vans_step_static(const vans_params *p, const float *eps_dev, cons
     // contents never leak into this one; the range flag is not read here
     int *flag = (int *)(eps_pad + kStaticEpsFloats);
     if (vans::launch_pad_eps(d, eps_dev, eps_pad, flag, s) != cudaSuccess) return VANS_ERR_CUDA;
-    const vans::Launch L = (p->q == 9) ? vans::Launch{4, 4, 1} : vans::Launch{2, 4, 1};
+    const vans::Launch L = (p->q == 9) ? vans::Launch{4, 4, 1, 0} : vans::Launch{2, 4, 1, 0};
     if (vans::launch_step(p->q, d, state_in, state_out, L, s) != cudaSuccess) return VANS_ERR_CUDA;
     return VANS_OK;
 }

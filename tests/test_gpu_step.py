@@ -21,15 +21,20 @@ def _case(q, shape, wall_mask, seed, tau=0.7, k_mode=0):
 
 STEP_CASES = [
     # q, (nz, ny, nx), wall_mask, launches
-    (9, (1, 13, 37), 2, [Launch(1, 1, 2), Launch(2, 2, 1), Launch(4, 1, 2), Launch(4, 4, 1)]),
-    (9, (1, 6, 5), 0, [Launch(4, 2, 1), Launch(1, 2, 1)]),
-    (9, (1, 1, 1), 0, [Launch(4, 2, 1)]),
-    (9, (1, 1, 3), 2, [Launch(1, 2, 1)]),
-    (9, (1, 9, 300), 2, [Launch(2, 2, 2), Launch(4, 2, 1)]),
-    (19, (7, 9, 21), 6, [Launch(1, 2, 1), Launch(2, 2, 2), Launch(4, 1, 2)]),
-    (19, (5, 4, 33), 2, [Launch(2, 2, 1)]),
-    (19, (3, 3, 4), 0, [Launch(1, 2, 1)]),
-    (19, (1, 1, 2), 6, [Launch(1, 2, 1)]),
+    (9, (1, 13, 37), 2, [Launch(1, 1, 2), Launch(2, 2, 1), Launch(4, 1, 2), Launch(4, 4, 1),
+                         Launch(2, 4, 3, 1), Launch(1, 8, 2, 1), Launch(2, 4, 3, 2)]),
+    (9, (1, 6, 5), 0, [Launch(4, 2, 1), Launch(1, 2, 1), Launch(4, 4, 2, 1), Launch(1, 8, 2, 2)]),
+    (9, (1, 1, 1), 0, [Launch(4, 2, 1), Launch(2, 4, 3, 1), Launch(2, 4, 3, 2)]),
+    (9, (1, 1, 3), 2, [Launch(1, 2, 1), Launch(2, 8, 3, 1), Launch(2, 8, 2, 2)]),
+    (9, (1, 9, 300), 2, [Launch(2, 2, 2), Launch(4, 2, 1), Launch(2, 4, 4, 1), Launch(1, 8, 4, 1),
+                         Launch(4, 4, 3, 2), Launch(1, 8, 4, 2)]),
+    (9, (1, 7, 1100), 0, [Launch(2, 4, 3, 1), Launch(4, 4, 3, 1), Launch(2, 4, 4, 2)]),
+    (9, (1, 40, 700), 2, [Launch(2, 8, 3, 2), Launch(1, 8, 5, 2)]),
+    (19, (7, 9, 21), 6, [Launch(1, 2, 1), Launch(2, 2, 2), Launch(4, 1, 2), Launch(1, 4, 3, 1),
+                         Launch(2, 4, 2, 1)]),
+    (19, (5, 4, 33), 2, [Launch(2, 2, 1), Launch(1, 8, 3, 1)]),
+    (19, (3, 3, 4), 0, [Launch(1, 2, 1), Launch(1, 4, 4, 1)]),
+    (19, (1, 1, 2), 6, [Launch(1, 2, 1), Launch(1, 4, 3, 1)]),
 ]
 
 
@@ -90,13 +95,14 @@ def test_d3q19_duct_downsized():
     assert np.abs(rho - rho_o).max() <= 1e-5
 
 
-def test_graph_replay_equals_single_launches():
+@pytest.mark.parametrize("L", [Launch(4, 4, 1), Launch(2, 4, 3, 1), Launch(2, 8, 3, 2)])
+def test_graph_replay_equals_single_launches(L):
     """vans_step(n) replays a captured CUDA graph for long runs; the result is
     bit-identical to n single steps."""
     torch = torch_cuda()
     p, eps, n = W.periodic_2d_shape(70, 50, nsteps=0)
-    a = solver(p, eps)
-    b = solver(p, eps)
+    a = solver(p, eps, launch=L)
+    b = solver(p, eps, launch=L)
     a.step(64 * 2 + 3)
     for _ in range(64 * 2 + 3):
         b.step(1)
@@ -134,7 +140,7 @@ def test_autotune_leaves_state_unchanged():
     a.step(10)
     b.step(10)
     L = a.autotune()
-    assert L.cpt in (1, 2, 4)
+    assert L.cpt in (1, 2, 4) and L.kind in (0, 1, 2)
     b.launch = L
     a.step(10)
     b.step(10)
@@ -156,7 +162,8 @@ def test_populations_roundtrip():
 def test_launch_shapes_agree_on_a_long_run():
     p, eps, n = W.periodic_2d_shape(150, 40, nsteps=300)
     ref = None
-    for L in (Launch(1, 2, 1), Launch(2, 4, 2), Launch(4, 4, 1), Launch(4, 2, 4)):
+    for L in (Launch(1, 2, 1), Launch(2, 4, 2), Launch(4, 4, 1), Launch(4, 2, 4),
+              Launch(2, 4, 3, 1), Launch(1, 8, 4, 1), Launch(4, 4, 2, 1), Launch(2, 8, 3, 2)):
         rho, u, f = gpu_run(p, eps, n, launch=L)
         if ref is None:
             ref = u
