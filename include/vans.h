@@ -80,9 +80,9 @@ typedef struct {
  * kind 1: bulk-copy pipeline kernel (persistent CTAs, rows staged in shared
  *         memory by cp.async.bulk): 32*warps threads (warps 4 or 8), cpt cells
  *         per thread per tile (1, 2, 4), `rows` = pipeline stages (2..6).
- * kind 2: D2Q9 only: the kind-1 pipeline where each CTA walks a vertical strip
- *         of tiles and keeps the porosity rows in a shared-memory ring, so each
- *         eps row is read from HBM once per strip.
+ * kind 2: the kind-1 pipeline where each CTA walks a strip of consecutive rows
+ *         (one column block, one z plane) and keeps the porosity rows in a
+ *         shared-memory ring, so each eps row is read from HBM once per strip.
  *         Kinds 1 and 2 are not available to the batched path. */
 typedef struct {
     int cpt;
@@ -160,8 +160,12 @@ int vans_set_launch(vans_t h, const vans_launch *cfg);
 /* -------------------------------------------------------------- adjoint -- */
 /* Reverse mode for J = sum over the plane x = x_out of eps*rho*u_x (Eq. 1moment)
  * at the final step.  A "lambda" buffer has the state layout and holds dJ/df*
- * of the populations a state buffer stores.  grad_acc is dense, (1 + D) * N
- * floats: dJ/deps(x) collected so far, then dJ/d(grad eps)(x) per component. */
+ * of the populations a state buffer stores.  grad_acc is dense, 2 * (1 + D) * N
+ * floats: the running sums of dJ/deps(x) and of dJ/d(grad eps)(x) per
+ * component ((1 + D) * N floats), then their FP32 compensation words (same
+ * layout): the accumulation is compensated (Neumaier), because dJ/deps is a
+ * small residual of large grad-eps sensitivities that cancel in the
+ * transposed stencil. */
 
 /* J of a state buffer (NULL = the current state) written to J_dev[0] (FP32,
  * fixed-order reduction).  Errors: VANS_ERR_ARG for x_out outside [0, nx). */
@@ -176,6 +180,24 @@ int vans_flux_seed(vans_t h, const float *state, int x_out, float *lam_dev, floa
  * into grad_acc.  state_t, lam_in and lam_out must be distinct buffers. */
 int vans_step_adjoint(vans_t h, const float *state_t, const float *lam_in, float *lam_out,
                       float *grad_acc);
+
+/* The reverse pass over one checkpointed segment in one call: copies the
+ * checkpoint `ckpt` (a state) into seg[0], recomputes len >= 1 forward steps
+ * seg[k] -> seg[k+1] with the step kernel (so the states equal the forward
+ * run's), then applies len reverse steps from seg[len-1] down to seg[0].  On
+ * entry lam holds the lambda of seg[len]; on return the lambda of seg[0].  seg
+ * is (len+1) state buffers back to back; tmp is a second lambda buffer; the
+ * eps partials are added into grad_acc.  The work is captured once per
+ * (buffers, len) into a CUDA graph and replayed on later calls. */
+int vans_adjoint_segment(vans_t h, const float *ckpt, float *seg, int len, float *lam, float *tmp,
+                         float *grad_acc);
+
+/* Arithmetic of the per-cell reverse step: 32 (FP32, the default) or 64 (FP64;
+ * loads, stores and the compensated accumulation stay FP32).  The eps gradient
+ * is a small residual of large grad-eps sensitivities, so FP32 per-cell
+ * rounding limits its relative accuracy on long rollouts.  VANS_ERR_ARG for
+ * other values. */
+int vans_set_adjoint_precision(vans_t h, int bits);
 
 /* dJ/deps (dense, N floats) from the lambda of the initial state and grad_acc:
  * adds the initial condition f = w eps and the transposed grad-eps stencil. */

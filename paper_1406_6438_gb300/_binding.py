@@ -135,6 +135,8 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
             "vans_flux_seed": (ctypes.c_int, [_H, _F, ctypes.c_int, _F, _F]),
             "vans_step_adjoint": (ctypes.c_int, [_H, _F, _F, _F, _F]),
             "vans_grad_finalize": (ctypes.c_int, [_H, _F, _F, _F]),
+            "vans_adjoint_segment": (ctypes.c_int, [_H, _F, _F, ctypes.c_int, _F, _F, _F]),
+            "vans_set_adjoint_precision": (ctypes.c_int, [_H, ctypes.c_int]),
             "vans_batch_workspace_bytes": (ctypes.c_size_t, [_P, ctypes.c_int]),
             "vans_batch_create": (ctypes.c_int, [_P, ctypes.c_int, _F, ctypes.c_size_t,
                                                  ctypes.c_void_p, ctypes.POINTER(_H)]),
@@ -309,7 +311,8 @@ class Solver:
 
     # -- reverse mode ---------------------------------------------------------
     def grad_floats(self) -> int:
-        return (1 + self.params.dim) * self.params.cells
+        """Floats of grad_acc: sums and compensation words of dJ/deps and dJ/d(grad eps)."""
+        return 2 * (1 + self.params.dim) * self.params.cells
 
     def flux(self, x_out: int, state=None, out=None):
         torch = _torch()
@@ -332,6 +335,20 @@ class Solver:
                                           _f32(lam_out, self.state_floats, "lam_out"),
                                           _f32(grad, self.grad_floats(), "grad_acc")),
                "vans_step_adjoint")
+
+    def set_adjoint_precision(self, bits: int):
+        _check(self.lib.vans_set_adjoint_precision(self._h, int(bits)), "vans_set_adjoint_precision")
+
+    def adjoint_segment(self, ckpt, seg, length: int, lam, tmp, grad):
+        """Recompute a segment from its checkpoint and walk lam back through it."""
+        if seg.numel() < (length + 1) * self.state_floats or seg.dtype != _torch().float32:
+            raise ValueError("seg: expected (length+1) float32 state buffers")
+        _check(self.lib.vans_adjoint_segment(self._h, _f32(ckpt, self.state_floats, "ckpt"),
+                                             _ptr(seg), int(length),
+                                             _f32(lam, self.state_floats, "lam"),
+                                             _f32(tmp, self.state_floats, "tmp"),
+                                             _f32(grad, self.grad_floats(), "grad_acc")),
+               "vans_adjoint_segment")
 
     def grad_finalize(self, lam0, grad, out=None):
         torch = _torch()

@@ -4,7 +4,8 @@
 ``nsteps`` steps of the porous LBM from rest and returns the outlet flux
 J = sum over the plane x = x_out of eps*rho*u_x (Eq. 1moment) at the last step,
 keeping a checkpoint of the state every ``every`` steps.  Its backward walks
-the segments newest first: it restores the segment's checkpoint, recomputes the
+the segments newest first: for each, one library call (vans_adjoint_segment,
+a CUDA graph replayed per segment) restores the checkpoint, recomputes the
 segment's states with the same step kernel (so they are bit-identical to the
 forward ones), then applies the hand-written adjoint step kernel to them in
 reverse, accumulating dJ/deps; a final kernel adds the initial condition
@@ -45,23 +46,21 @@ class OutletFlux(torch.autograd.Function):
         lam_b = solver.new_state()
         grad = torch.empty(solver.grad_floats(), dtype=torch.float32, device=solver.device)
         solver.flux_seed(x_out, lam_a, grad, state=ctx.final)
-        seg = torch.empty((every + 1, solver.state_floats), dtype=torch.float32,
+        seg = torch.zeros((every + 1, solver.state_floats), dtype=torch.float32,
                           device=solver.device)
         for s in reversed(range(len(ctx.ckpts))):
             start = s * every
             length = min(every, nsteps - start)
-            seg[0].copy_(ctx.ckpts[s])
-            for k in range(length):
-                solver.step_raw(seg[k], seg[k + 1])
-            for k in reversed(range(length)):
-                solver.step_adjoint(seg[k], lam_a, lam_b, grad)
-                lam_a, lam_b = lam_b, lam_a
+            # checkpoint -> recompute -> reverse sweep, one captured graph per segment shape
+            solver.adjoint_segment(ctx.ckpts[s], seg, length, lam_a, lam_b, grad)
         dJ = solver.grad_finalize(lam_a, grad)
         return (dJ.view(ctx.shape) * gJ), None, None, None, None
 
 
 def outlet_flux(eps, solver: Solver, nsteps: int, every: int = 100, x_out: int | None = None):
-    """J(eps) with a gradient; x_out defaults to the last plane, nx - 1."""
+    """J(eps) with a gradient; x_out defaults to the last plane, nx - 1.  The
+    reverse step runs in the precision set by ``solver.set_adjoint_precision``
+    (32 by default; 64 for FP64 per-cell arithmetic on long rollouts)."""
     if x_out is None:
         x_out = solver.params.nx - 1
     return OutletFlux.apply(eps, solver, int(nsteps), int(every), int(x_out))

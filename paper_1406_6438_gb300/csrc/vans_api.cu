@@ -107,8 +107,6 @@ bool launch_ok(const vans_launch *c, int q, bool batched) {
     if (c->rows < 2 || c->rows > 6) return false;
     // the instantiated pipeline shapes
     const int nt = 32 * c->warps;
-    if (c->kind == 2)
-        return q == 9 && ((nt == 128 && (c->cpt == 2 || c->cpt == 4)) || (nt == 256 && c->cpt <= 2));
     if (q == 9)
         return (nt == 128 && (c->cpt == 2 || c->cpt == 4)) || (nt == 256 && c->cpt <= 2);
     return (nt == 128 && c->cpt <= 2) || (nt == 256 && c->cpt == 1);
@@ -126,6 +124,7 @@ struct vans_s {
     Launch L{4, 4, 1, 0};
     cudaGraphExec_t gexec = nullptr;
     int *flag = nullptr;                        // device status words (workspace)
+    int adj_fp64 = 0;                           // reverse-step arithmetic in FP64
     // single domain
     vans_params p{};
     VDom dom{};
@@ -145,6 +144,14 @@ struct vans_s {
     int grid = 0;
     int parity = 0;
     std::vector<char> dom_ready;
+    // captured reverse-pass segments (adjoint), keyed by their buffers and length
+    struct SegGraph {
+        const float *seg;
+        int len;
+        const float *lam, *tmp, *grad;
+        cudaGraphExec_t exec;
+    };
+    std::vector<SegGraph> seg_graphs;
 };
 
 namespace {
@@ -156,6 +163,8 @@ void drop_graph(vans_t h) {
         cudaGraphExecDestroy(h->gexec);
         h->gexec = nullptr;
     }
+    for (auto &g : h->seg_graphs) cudaGraphExecDestroy(g.exec);
+    h->seg_graphs.clear();
 }
 
 cudaError_t one_step(vans_t h, cudaStream_t s, int par) {
@@ -301,8 +310,9 @@ std::vector<Launch> candidates(int q, bool batched) {
         c.insert(c.end(), t, t + 14);
     } else {
         const Launch t[] = {{1, 4, 3, 1}, {1, 4, 4, 1}, {2, 4, 2, 1}, {2, 4, 3, 1},
-                            {1, 8, 2, 1}, {1, 8, 3, 1}};
-        c.insert(c.end(), t, t + 6);
+                            {1, 8, 2, 1}, {1, 8, 3, 1}, {1, 4, 3, 2}, {2, 4, 2, 2},
+                            {2, 4, 3, 2}, {1, 8, 2, 2}, {1, 8, 3, 2}};
+        c.insert(c.end(), t, t + 11);
     }
     return c;
 }
@@ -502,11 +512,12 @@ int vans_flux_seed(vans_t h, const float *state, int x_out, float *lam_dev, floa
     const int D = h->q == 9 ? 2 : 3;
     if (cudaMemsetAsync(lam_dev, 0, h->sfloats * sizeof(float), h->stream) != cudaSuccess)
         return VANS_ERR_CUDA;
-    if (cudaMemsetAsync(grad_acc, 0, (1 + D) * h->dom.cells * sizeof(float), h->stream) != cudaSuccess)
+    if (cudaMemsetAsync(grad_acc, 0, 2 * (1 + D) * h->dom.cells * sizeof(float), h->stream) !=
+        cudaSuccess)
         return VANS_ERR_CUDA;
     ++h->launches;
     return cuda_status(vans::launch_flux_seed(h->q, h->dom, state ? state : h->st[h->cur], x_out,
-                                              lam_dev, grad_acc, h->stream));
+                                              lam_dev, grad_acc, h->adj_fp64, h->stream));
 }
 
 int vans_step_adjoint(vans_t h, const float *state_t, const float *lam_in, float *lam_out,
@@ -515,8 +526,70 @@ int vans_step_adjoint(vans_t h, const float *state_t, const float *lam_in, float
     if (lam_in == lam_out || (const float *)lam_out == state_t) return VANS_ERR_ARG;
     if (!h->eps_set) return VANS_ERR_STATE;
     ++h->launches;
-    return cuda_status(
-        vans::launch_step_adjoint(h->q, h->dom, state_t, lam_in, lam_out, grad_acc, h->stream));
+    return cuda_status(vans::launch_step_adjoint(h->q, h->dom, state_t, lam_in, lam_out, grad_acc,
+                                                 h->adj_fp64, h->stream));
+}
+
+int vans_adjoint_segment(vans_t h, const float *ckpt, float *seg, int len, float *lam, float *tmp,
+                         float *grad_acc) {
+    if (!h || h->batched || !ckpt || !seg || !lam || !tmp || !grad_acc || len < 1) return VANS_ERR_ARG;
+    if (lam == tmp) return VANS_ERR_ARG;
+    if (!h->eps_set) return VANS_ERR_STATE;
+    const long long sf = h->sfloats;
+    if (cudaMemcpyAsync(seg, ckpt, sf * sizeof(float), cudaMemcpyDeviceToDevice, h->stream) !=
+        cudaSuccess)
+        return VANS_ERR_CUDA;
+    vans_s::SegGraph *g = nullptr;
+    for (auto &e : h->seg_graphs)
+        if (e.seg == seg && e.len == len && e.lam == lam && e.tmp == tmp && e.grad == grad_acc) g = &e;
+    if (!g) {
+        if (h->seg_graphs.size() >= 4) {
+            cudaGraphExecDestroy(h->seg_graphs.front().exec);
+            h->seg_graphs.erase(h->seg_graphs.begin());
+        }
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return VANS_ERR_CUDA;
+        cudaError_t le = cudaSuccess;
+        // recompute the segment's states with the forward step kernel
+        for (int k = 0; k < len && le == cudaSuccess; ++k)
+            le = vans::launch_step(h->q, h->dom, seg + k * sf, seg + (k + 1) * sf, h->L, h->cap);
+        // then walk back through them
+        float *a = lam, *b = tmp;
+        for (int k = len - 1; k >= 0 && le == cudaSuccess; --k) {
+            le = vans::launch_step_adjoint(h->q, h->dom, seg + k * sf, a, b, grad_acc, h->adj_fp64,
+                                           h->cap);
+            float *t = a;
+            a = b;
+            b = t;
+        }
+        if (le == cudaSuccess && a != lam)
+            le = cudaMemcpyAsync(lam, a, sf * sizeof(float), cudaMemcpyDeviceToDevice, h->cap);
+        cudaError_t e = cudaStreamEndCapture(h->cap, &graph);
+        if (le != cudaSuccess || e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return VANS_ERR_CUDA;
+        }
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return VANS_ERR_CUDA;
+        h->seg_graphs.push_back(vans_s::SegGraph{seg, len, lam, tmp, grad_acc, exec});
+        g = &h->seg_graphs.back();
+    }
+    if (cudaGraphLaunch(g->exec, h->stream) != cudaSuccess) return VANS_ERR_CUDA;
+    h->launches += 2LL * len;
+    return VANS_OK;
+}
+
+int vans_set_adjoint_precision(vans_t h, int bits) {
+    if (!h || (bits != 32 && bits != 64)) return VANS_ERR_ARG;
+    const int v = (bits == 64);
+    if (v != h->adj_fp64) {
+        h->adj_fp64 = v;
+        drop_graph(h);
+    }
+    return VANS_OK;
 }
 
 int vans_grad_finalize(vans_t h, const float *lam0, const float *grad_acc, float *dJdeps_dev) {

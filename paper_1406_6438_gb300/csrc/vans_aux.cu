@@ -1,5 +1,6 @@
 // vans_aux.cu -- everything around the step: porosity set-up, moments, state
 // import/export, divergence check, outlet flux, and the reverse-mode adjoint.
+#include "vans_adjoint.cuh"
 #include "vans_device.cuh"
 
 namespace vans {
@@ -159,135 +160,17 @@ __global__ void k_check(const VDom d, const float *__restrict__ st, int *flag) {
 }
 
 // ------------------------------------------------------ reverse mode -----
-// Reverse of macro(): given dJ/dR, dJ/du and dJ/dV, returns the part of dJ/dh_i
-// common to all i (lam0) plus e_i . jbar, and the partial derivatives of J with
-// respect to eps(x) (at fixed f) and grad eps(x).
-template <int Q>
-__device__ __forceinline__ void macro_vjp(const VDom &d, const Macro<Q> &M, float Rbar,
-                                          float ubar[3], const float Vbar[3], float &lam0,
-                                          float jbar[3], float &ebar, float gbar[3]) {
-    constexpr int D = Lat<Q>::D;
-    float Pcbar[3], Fbar[3], mbar[3];
-    float Fu = 0.f;
-    // V = Pc + F,  F = R g - alpha u - beta |u| u
-#pragma unroll
-    for (int c = 0; c < D; ++c) {
-        Pcbar[c] = Vbar[c];
-        Fbar[c] = Vbar[c];
-        Rbar += Fbar[c] * d.g[c];
-        Fu += Fbar[c] * M.u[c];
-    }
-    float alphabar = -Fu;
-    float betabar = -M.un * Fu;
-    const float kd = M.alpha + M.beta * M.un;
-    const float ib = (M.un > 0.f) ? M.beta * Fu / M.un : 0.f;
-    float ubu = 0.f;
-#pragma unroll
-    for (int c = 0; c < D; ++c) {
-        ubar[c] += -kd * Fbar[c] - ib * M.u[c];
-        ubu += ubar[c] * M.u[c];
-    }
-    // u = m * 2/D,  D = a + sqrt(a^2 + 4 b |m|)
-    const float Dbar = -ubu / M.D;
-    const float abar = Dbar * (1.f + M.a / M.sq);
-    const float bbar = Dbar * 2.f * M.mm / M.sq;
-    const float mmbar = Dbar * 2.f * M.b / M.sq;
-    const float im = (M.mm > 0.f) ? mmbar / M.mm : 0.f;
-#pragma unroll
-    for (int c = 0; c < D; ++c) mbar[c] = ubar[c] * M.s + im * M.m[c];
-    // a = R + alpha/2, b = beta/2
-    Rbar += abar;
-    alphabar += 0.5f * abar;
-    betabar += 0.5f * bbar;
-    // m = j + Pc/2 + R g/2
-    float rhobar = 0.f;
-#pragma unroll
-    for (int c = 0; c < D; ++c) {
-        jbar[c] = mbar[c];
-        Pcbar[c] += 0.5f * mbar[c];
-        Rbar += 0.5f * mbar[c] * d.g[c];
-        // Pc = rho grad eps / 3
-        rhobar += (1.f / 3.f) * Pcbar[c] * M.ge[c];
-        gbar[c] = (1.f / 3.f) * M.rho * Pcbar[c];
-    }
-    // rho = R / eps
-    Rbar += rhobar * M.inv_e;
-    ebar = -rhobar * M.R * M.inv_e * M.inv_e;
-    float al, be, da, db;
-    drag<true>(d, M.e0, M.inv_e, al, be, &da, &db);
-    ebar += alphabar * da + betabar * db;
-    lam0 = Rbar;
-}
-
-// Reverse of the collision of one cell.  mu_i = dJ/df*_i; returns lam_i =
-// dJ/df_i, the eps partial and the grad-eps partial.  With M_i = mu_i w_i,
-// SM = sum M_i, SMe = sum M_i e_i and T = sum M_i e_i e_i^T, the adjoints of
-// f^eq (Eq. d2q9eq) and of P_i + F_i (Eqs. pi, Fi) reduce to
-//   Rbar = omega (SM + 3 SMe.u + 4.5 u.T.u - 1.5 u.u SM)
-//   ubar = omega R (3 SMe + 9 T u - 3 u SM) + ct (9 T V - 3 V SM)
-//   Vbar = ct (3 SMe - 3 u SM + 9 T u).
-template <int Q>
-__device__ __forceinline__ void collide_vjp(const VDom &d, const float h[Q], float e0,
-                                            const float et[Q], const float mu[Q], float lam[Q],
-                                            float &ebar, float gbar[3]) {
-    using L = Lat<Q>;
-    constexpr int D = L::D;
-    Macro<Q> M;
-    macro<Q>(d, h, e0, et, M);
-    float SM = 0.f, SMe[3] = {0.f, 0.f, 0.f}, T[3][3] = {{0.f}};
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const float Mi = mu[i] * L::w(i);
-        const int e[3] = {L::ex(i), L::ey(i), L::ez(i)};
-        SM += Mi;
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-            if (e[a] == 0) continue;
-            SMe[a] += e[a] * Mi;
-#pragma unroll
-            for (int b = a; b < D; ++b)
-                if (e[b] != 0) T[a][b] += (e[a] * e[b]) * Mi;
-        }
-    }
-#pragma unroll
-    for (int a = 0; a < D; ++a)
-#pragma unroll
-        for (int b = 0; b < a; ++b) T[a][b] = T[b][a];
-    float Tu[3], TV[3], uu = 0.f, SMeu = 0.f, uTu = 0.f;
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-        Tu[a] = 0.f;
-        TV[a] = 0.f;
-#pragma unroll
-        for (int b = 0; b < D; ++b) {
-            Tu[a] += T[a][b] * M.u[b];
-            TV[a] += T[a][b] * M.V[b];
-        }
-        uu += M.u[a] * M.u[a];
-        SMeu += SMe[a] * M.u[a];
-    }
-#pragma unroll
-    for (int a = 0; a < D; ++a) uTu += M.u[a] * Tu[a];
-    const float om = d.omega, ct = d.ctau;
-    const float Rbar = om * (SM + 3.f * SMeu + 4.5f * uTu - 1.5f * uu * SM);
-    float ubar[3], Vbar[3];
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-        ubar[a] = om * M.R * (3.f * SMe[a] + 9.f * Tu[a] - 3.f * M.u[a] * SM) +
-                  ct * (9.f * TV[a] - 3.f * M.V[a] * SM);
-        Vbar[a] = ct * (3.f * SMe[a] - 3.f * M.u[a] * SM + 9.f * Tu[a]);
-    }
-    float lam0, jbar[3];
-    macro_vjp<Q>(d, M, Rbar, ubar, Vbar, lam0, jbar, ebar, gbar);
-    const float om1 = 1.f - om;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        float l = om1 * mu[i] + lam0;
-        if (L::ex(i)) l += L::ex(i) * jbar[0];
-        if (L::ey(i)) l += L::ey(i) * jbar[1];
-        if (D == 3 && L::ez(i)) l += L::ez(i) * jbar[2];
-        lam[i] = l;
-    }
+// Compensated (Neumaier) FP32 accumulation: *s holds the running sum and *c the
+// rounding error lost so far; s + c is the sum to about one FP32 ulp however
+// many steps are added.  The eps gradient is a small residual of large
+// grad-eps sensitivities (they cancel through the transposed stencil), so the
+// plain FP32 running sum would lose most of it over thousands of steps.
+__device__ __forceinline__ void acc2(float *s, float *c, float x) {
+    const float a = *s;
+    const float t = a + x;
+    const float e = (fabsf(a) >= fabsf(x)) ? (a - t) + x : (x - t) + a;
+    *s = t;
+    *c += e;
 }
 
 // J = sum over the plane x = x_out of eps rho u_x; one block, fixed-order sum.
@@ -317,7 +200,7 @@ __global__ void __launch_bounds__(256) k_flux(const VDom d, const float *__restr
 
 // Seed of the reverse pass: lambda at the entries the outlet cells pull, and
 // the direct eps / grad-eps partials of J.  lam and grad are zeroed beforehand.
-template <int Q>
+template <int Q, typename T>
 __global__ void k_flux_seed(const VDom d, const float *__restrict__ st, int x_out,
                             float *__restrict__ lam, float *__restrict__ grad) {
     using L = Lat<Q>;
@@ -329,24 +212,24 @@ __global__ void k_flux_seed(const VDom d, const float *__restrict__ st, int x_ou
         float h[Q], e0, et[Q];
         pull_cell<Q>(d, st, x_out, y, z, Y, Z, h);
         eps_cell<Q>(d, x_out, y, z, Y, Z, e0, et);
-        Macro<Q> M;
-        macro<Q>(d, h, e0, et, M);
+        MacroT<Q, T> M;
+        macro_t<Q, T>(d, h, e0, et, M);
         // J_cell = R u_x
-        float ubar[3] = {M.R, 0.f, 0.f}, Vbar[3] = {0.f, 0.f, 0.f};
-        float lam0, jbar[3], ebar, gbar[3];
-        macro_vjp<Q>(d, M, M.u[0], ubar, Vbar, lam0, jbar, ebar, gbar);
+        T ubar[3] = {M.R, T(0), T(0)}, Vbar[3] = {T(0), T(0), T(0)};
+        T lam0, jbar[3], ebar, gbar[3];
+        macro_vjp_t<Q, T>(d, M, M.u[0], ubar, Vbar, lam0, jbar, ebar, gbar);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            float l = lam0;
+            T l = lam0;
             if (L::ex(i)) l += L::ex(i) * jbar[0];
             if (L::ey(i)) l += L::ey(i) * jbar[1];
             if (D == 3 && L::ez(i)) l += L::ez(i) * jbar[2];
-            lam[pull_index<Q>(d, i, x_out, y, z, Y, Z)] = l;
+            lam[pull_index<Q>(d, i, x_out, y, z, Y, Z)] = (float)l;
         }
         const long long n = (long long)r * d.nx + x_out;
-        grad[n] = ebar;
+        grad[n] = (float)ebar;       // sums; the compensations were zeroed with them
 #pragma unroll
-        for (int c = 0; c < D; ++c) grad[(1 + c) * d.cells + n] = gbar[c];
+        for (int c = 0; c < D; ++c) grad[(1 + c) * d.cells + n] = (float)gbar[c];
     }
 }
 
@@ -355,7 +238,7 @@ __global__ void k_flux_seed(const VDom d, const float *__restrict__ st, int x_ou
 // the step's outputs is read where the step wrote the copy that is streamed on
 // (the halo column at the periodic seam); the result is scattered to the very
 // entries the pull read, so the scatter is a permutation and needs no atomics.
-template <int Q, int CPT, bool EDGE>
+template <int Q, int CPT, bool EDGE, typename T>
 __device__ __forceinline__ void adj_row(const VDom &d, const float *__restrict__ st,
                                         const float *__restrict__ lin, float *__restrict__ lout,
                                         float *__restrict__ grad, int y, int z, int x0, int lane) {
@@ -421,15 +304,17 @@ __device__ __forceinline__ void adj_row(const VDom &d, const float *__restrict__
             const bool wall = Y.wall[1 + L::ey(i)] || Z.wall[1 + L::ez(i)];
             et[i] = (i == 0 || wall) ? e0 : E[1 + L::ey(i)][1 + L::ez(i)][k + 1 + L::ex(i)];
         }
-        float ebar, gbar[3];
-        collide_vjp<Q>(d, hh, e0, et, mm, ll, ebar, gbar);
+        T ebar, gbar[3];
+        collide_vjp_t<Q, T>(d, hh, e0, et, mm, ll, ebar, gbar);
 #pragma unroll
         for (int i = 0; i < Q; ++i) lam[i][k] = ll[i];
         if (x0 + k < d.nx) {
             const long long n = ((long long)z * d.ny + y) * d.nx + x0 + k;
-            grad[n] += ebar;
+            const long long nc = (1 + D) * d.cells;   // compensation words follow the sums
+            acc2(&grad[n], &grad[nc + n], (float)ebar);
 #pragma unroll
-            for (int c = 0; c < D; ++c) grad[(1 + c) * d.cells + n] += gbar[c];
+            for (int c = 0; c < D; ++c)
+                acc2(&grad[(1 + c) * d.cells + n], &grad[nc + (1 + c) * d.cells + n], (float)gbar[c]);
         }
     }
 #pragma unroll
@@ -442,7 +327,7 @@ __device__ __forceinline__ void adj_row(const VDom &d, const float *__restrict__
     }
 }
 
-template <int Q, int CPT>
+template <int Q, int CPT, typename T>
 __global__ void __launch_bounds__(256) k_step_adjoint(const VDom d, const float *__restrict__ st,
                                                       const float *__restrict__ lin,
                                                       float *__restrict__ lout,
@@ -459,27 +344,34 @@ __global__ void __launch_bounds__(256) k_step_adjoint(const VDom d, const float 
     const int y = r % d.ny, z = r / d.ny;
     const bool edge = (y == 0) || (y == d.ny - 1) || (Q == 19 && (z == 0 || z == d.nz - 1));
     if (edge)
-        adj_row<Q, CPT, true>(d, st, lin, lout, grad, y, z, x0, lane);
+        adj_row<Q, CPT, true, T>(d, st, lin, lout, grad, y, z, x0, lane);
     else
-        adj_row<Q, CPT, false>(d, st, lin, lout, grad, y, z, x0, lane);
+        adj_row<Q, CPT, false, T>(d, st, lin, lout, grad, y, z, x0, lane);
 }
 
 // dJ/deps = G_eps + sum_i w_i lambda_i(0) (from f(0) = w eps) + the transposed
-// grad-eps stencil applied to G_grad.
+// grad-eps stencil applied to G_grad.  Runs once per reverse pass; it combines
+// each compensated accumulator (sum + compensation) and evaluates the stencil,
+// whose terms cancel to a much smaller result, in FP64.
 template <int Q>
 __global__ void k_grad_finalize(const VDom d, const float *__restrict__ lam0,
                                 const float *__restrict__ grad, float *__restrict__ out) {
     using L = Lat<Q>;
     constexpr int D = L::D;
+    const long long nc = (1 + D) * d.cells;
+    auto G = [&](int comp, long long m) -> double {
+        return (double)grad[comp * d.cells + m] + (double)grad[nc + comp * d.cells + m];
+    };
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < d.cells;
          n += (long long)gridDim.x * blockDim.x) {
         int x, y, z;
         cell_xyz(d, n, x, y, z);
         Nb3 Y, Z;
         nb_yz<Q>(d, y, z, Y, Z);
-        float v = grad[n];
+        double v = G(0, n);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) v += L::w(i) * lam0[pull_index<Q>(d, i, x, y, z, Y, Z)];
+        for (int i = 0; i < Q; ++i)
+            v += (double)L::w(i) * (double)lam0[pull_index<Q>(d, i, x, y, z, Y, Z)];
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
             const int e[3] = {L::ex(i), L::ey(i), L::ez(i)};
@@ -488,20 +380,20 @@ __global__ void k_grad_finalize(const VDom d, const float *__restrict__ lam0,
                 int xs = x - e[0];
                 xs = xs < 0 ? xs + d.nx : (xs >= d.nx ? xs - d.nx : xs);
                 const long long m = ((long long)Z.r[1 - e[2]] * d.ny + Y.r[1 - e[1]]) * d.nx + xs;
-                float s = 0.f;
+                double s = 0.0;
 #pragma unroll
-                for (int c = 0; c < D; ++c) s += e[c] * grad[(1 + c) * d.cells + m];
-                v += 3.f * L::w(i) * s;
+                for (int c = 0; c < D; ++c) s += e[c] * G(1 + c, m);
+                v += 3.0 * (double)L::w(i) * s;
             }
             // x itself, whose neighbour x + e_i lies past a wall
             if (Y.wall[1 + e[1]] || Z.wall[1 + e[2]]) {
-                float s = 0.f;
+                double s = 0.0;
 #pragma unroll
-                for (int c = 0; c < D; ++c) s += e[c] * grad[(1 + c) * d.cells + n];
-                v += 3.f * L::w(i) * s;
+                for (int c = 0; c < D; ++c) s += e[c] * G(1 + c, n);
+                v += 3.0 * (double)L::w(i) * s;
             }
         }
-        out[n] = v;
+        out[n] = (float)v;
     }
 }
 
@@ -564,15 +456,19 @@ cudaError_t launch_flux(int q, const VDom &d, const float *state, int x_out, flo
 }
 
 cudaError_t launch_flux_seed(int q, const VDom &d, const float *state, int x_out, float *lam,
-                             float *grad, cudaStream_t s) {
+                             float *grad, int fp64, cudaStream_t s) {
     const int g = grid_for(d.rows, 256);
-    VANS_DISPATCH_Q(q, (k_flux_seed<9><<<g, 256, 0, s>>>(d, state, x_out, lam, grad)),
-                    (k_flux_seed<19><<<g, 256, 0, s>>>(d, state, x_out, lam, grad)));
+    if (fp64)
+        VANS_DISPATCH_Q(q, (k_flux_seed<9, double><<<g, 256, 0, s>>>(d, state, x_out, lam, grad)),
+                        (k_flux_seed<19, double><<<g, 256, 0, s>>>(d, state, x_out, lam, grad)));
+    else
+        VANS_DISPATCH_Q(q, (k_flux_seed<9, float><<<g, 256, 0, s>>>(d, state, x_out, lam, grad)),
+                        (k_flux_seed<19, float><<<g, 256, 0, s>>>(d, state, x_out, lam, grad)));
     return cudaGetLastError();
 }
 
 cudaError_t launch_step_adjoint(int q, const VDom &d, const float *state, const float *lam_in,
-                                float *lam_out, float *grad, cudaStream_t s) {
+                                float *lam_out, float *grad, int fp64, cudaStream_t s) {
     // two cells per lane for D2Q9, one for D3Q19 (register pressure); 4 warps x 2 rows
     const int warps = 4, rows = 2;
     const int cpt = (q == 9) ? 2 : 1;
@@ -580,8 +476,12 @@ cudaError_t launch_step_adjoint(int q, const VDom &d, const float *state, const 
     const int nrb = (d.rows + rows - 1) / rows;
     dim3 block(32 * warps, rows);
     const unsigned nb = (unsigned)((long long)nxb * nrb);
-    VANS_DISPATCH_Q(q, (k_step_adjoint<9, 2><<<nb, block, 0, s>>>(d, state, lam_in, lam_out, grad, nxb)),
-                    (k_step_adjoint<19, 1><<<nb, block, 0, s>>>(d, state, lam_in, lam_out, grad, nxb)));
+    if (fp64)
+        VANS_DISPATCH_Q(q, (k_step_adjoint<9, 2, double><<<nb, block, 0, s>>>(d, state, lam_in, lam_out, grad, nxb)),
+                        (k_step_adjoint<19, 1, double><<<nb, block, 0, s>>>(d, state, lam_in, lam_out, grad, nxb)));
+    else
+        VANS_DISPATCH_Q(q, (k_step_adjoint<9, 2, float><<<nb, block, 0, s>>>(d, state, lam_in, lam_out, grad, nxb)),
+                        (k_step_adjoint<19, 1, float><<<nb, block, 0, s>>>(d, state, lam_in, lam_out, grad, nxb)));
     return cudaGetLastError();
 }
 

@@ -65,9 +65,9 @@ cudaError_t launch_check(int q, const VDom &d, const float *state, int *flag, cu
 cudaError_t launch_flux(int q, const VDom &d, const float *state, int x_out, float *J,
                         cudaStream_t stream);
 cudaError_t launch_flux_seed(int q, const VDom &d, const float *state, int x_out, float *lam,
-                             float *grad, cudaStream_t stream);
+                             float *grad, int fp64, cudaStream_t stream);
 cudaError_t launch_step_adjoint(int q, const VDom &d, const float *state, const float *lam_in,
-                                float *lam_out, float *grad, cudaStream_t stream);
+                                float *lam_out, float *grad, int fp64, cudaStream_t stream);
 cudaError_t launch_grad_finalize(int q, const VDom &d, const float *lam0, const float *grad,
                                  float *dJ, cudaStream_t stream);
 

@@ -179,62 +179,77 @@ __global__ void __launch_bounds__(NT) k_step_tma(const VDom d, const float *__re
 }
 
 // ---------------------------------------------------------------------------
-// D2Q9 variant with a porosity ring.  Each CTA walks a vertical strip: one
-// column block xt and a run of consecutive rows r0..r1-1, so tile k needs the
-// eps rows r0+k-1, r0+k, r0+k+1 and only r0+k+1 is new.  The eps rows live in
-// a ring of stages+2 row slots next to the population stages; the producer
-// loads the one new row with each tile (the first tile also loads its two
+// Variant with a porosity ring.  Each CTA walks one strip: a column block xt,
+// one z plane and a run of consecutive rows y0..y1-1, so tile k (row y0+k)
+// needs the eps rows at y-1, y, y+1 (times z-1, z, z+1 for D3Q19) and only the
+// y+1 ones are new.  The eps rows live in a ring of stages+2 slots (a slot
+// holds the NZR = 1 or 3 z-rows of one y) beside the population stages; the
+// producer loads one slot per tile (the first tile also loads its two
 // predecessors), so each eps row leaves HBM once per strip instead of three
-// times.  Ring slot of eps row r0-1+j is j mod (stages+2); the slot a new row
-// overwrites was last read by tile k-stages, which has finished when tile k is
-// issued.
-template <int TW>
-__device__ __forceinline__ void issue_tile_ring(const VDom &d, const float *__restrict__ fin, int row,
-                                                int xs, int k, int r0, float *sb, float *ring,
+// (D2Q9) or nine (D3Q19) times.  Slot of y-position y0-1+j is j mod (stages+2);
+// the slot a new position overwrites was last read by tile k-stages, which has
+// finished when tile k is issued.
+template <int Q, int TW>
+__device__ __forceinline__ void issue_tile_ring(const VDom &d, const float *__restrict__ fin, int y,
+                                                int z, int xs, int k, int y0, float *sb, float *ring,
                                                 int rslots, uint64_t *bar) {
-    using L = Lat<9>;
+    using L = Lat<Q>;
     constexpr int SEG = TW + 8;
-    const int y = row;
+    constexpr int NZR = (Q == 9) ? 1 : 3;
     const Nb3 Y = nb3<true>(y, d.ny, d.wall_y);
+    Nb3 Z;
+    if (Q == 19) {
+        Z = nb3<true>(z, d.nz, d.wall_z);
+    } else {
+        Z.r[0] = Z.r[1] = Z.r[2] = 0;
+        Z.wall[0] = Z.wall[1] = Z.wall[2] = false;
+    }
     const int nval = min(TW, d.nx - xs);
     const uint32_t bytes = (uint32_t)((((nval + 3) & ~3) + 8) * 4);
-    const int neps = (k == 0) ? 3 : 1;
-    mbar_arrive_expect_tx(bar, bytes * (9 + neps));
+    const int jfirst = (k == 0) ? 0 : k + 2;
+    mbar_arrive_expect_tx(bar, bytes * (Q + NZR * (k + 3 - jfirst)));
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const int ey = L::ey(i);
-        const bool bb = Y.wall[1 - ey];
+    for (int i = 0; i < Q; ++i) {
+        const int ey = L::ey(i), ez = L::ez(i);
+        const bool bb = Y.wall[1 - ey] || Z.wall[1 - ez];
         const int si = bb ? L::opp(i) : i;
-        const long long ro = (long long)(bb ? y : Y.r[1 - ey]) * d.pitch + VANS_OFF;
+        const long long ro = bb ? row_offset(d, y, z) : row_offset(d, Y.r[1 - ey], Z.r[1 - ez]);
         bulk_g2s(sb + i * SEG, fin + si * d.plane + ro + xs - 4, bytes, bar);
     }
-    for (int j = (k == 0 ? 0 : k + 2); j <= k + 2; ++j) {
-        int ry = r0 - 1 + j;                      // eps row r0-1+j, wrapped into [0, ny)
+    for (int j = jfirst; j <= k + 2; ++j) {
+        int ry = y0 - 1 + j;                      // y-position y0-1+j, wrapped into [0, ny)
         ry = ry < 0 ? ry + d.ny : (ry >= d.ny ? ry - d.ny : ry);
-        bulk_g2s(ring + (j % rslots) * SEG, d.eps + (long long)ry * d.pitch + VANS_OFF + xs - 4, bytes,
-                 bar);
+        float *slot = ring + (j % rslots) * (NZR * SEG);
+#pragma unroll
+        for (int dz = 0; dz < NZR; ++dz) {
+            const int rz = (Q == 9) ? 0 : Z.r[dz];
+            bulk_g2s(slot + dz * SEG, d.eps + row_offset(d, ry, rz) + xs - 4, bytes, bar);
+        }
     }
 }
 
-template <int NT, int CPT>
+template <int Q, int NT, int CPT>
 __global__ void __launch_bounds__(NT) k_step_tma_ring(const VDom d, const float *__restrict__ fin,
-                                                      float *__restrict__ fout, int ntx, int per_col,
+                                                      float *__restrict__ fout, int ntx, int per_y,
                                                       int stages) {
-    using L = Lat<9>;
+    using L = Lat<Q>;
     constexpr int TW = NT * CPT;
     constexpr int SEG = TW + 8;
+    constexpr int NZR = (Q == 9) ? 1 : 3;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
     float *buf = reinterpret_cast<float *>(smem + kBarBytes);
-    float *ring = buf + stages * 9 * SEG;
+    float *ring = buf + stages * Q * SEG;
     const int rslots = stages + 2;
     const int tid = threadIdx.x;
-    // strip of this CTA: column block xt, rows [r0, r1)
+    // strip of this CTA: column block xt, plane z, rows [y0, y1)
     const int xt = blockIdx.x % ntx;
-    const int c = blockIdx.x / ntx;
-    const int r0 = (int)((long long)c * d.ny / per_col);
-    const int r1 = (int)((long long)(c + 1) * d.ny / per_col);
-    const int n = r1 - r0;
+    const int rem = blockIdx.x / ntx;
+    const int z = rem % d.nz;
+    const int yc = rem / d.nz;
+    const int y0 = (int)((long long)yc * d.ny / per_y);
+    const int y1 = (int)((long long)(yc + 1) * d.ny / per_y);
+    const int n = y1 - y0;
     if (n <= 0) return;
     const int xs = xt * TW;
 
@@ -246,7 +261,15 @@ __global__ void __launch_bounds__(NT) k_step_tma_ring(const VDom d, const float 
     if (tid == 0) {
         const int pre = n < stages ? n : stages;
         for (int k = 0; k < pre; ++k)
-            issue_tile_ring<TW>(d, fin, r0 + k, xs, k, r0, buf + k * 9 * SEG, ring, rslots, &bars[k]);
+            issue_tile_ring<Q, TW>(d, fin, y0 + k, z, xs, k, y0, buf + k * Q * SEG, ring, rslots,
+                                   &bars[k]);
+    }
+    Nb3 Z;
+    if (Q == 19) {
+        Z = nb3<true>(z, d.nz, d.wall_z);
+    } else {
+        Z.r[0] = Z.r[1] = Z.r[2] = 0;
+        Z.wall[0] = Z.wall[1] = Z.wall[2] = false;
     }
     int k = 0, s = 0;
     uint32_t par = 0;
@@ -254,43 +277,43 @@ __global__ void __launch_bounds__(NT) k_step_tma_ring(const VDom d, const float 
     for (; k < n; ++k) {
         ok = __syncthreads_and(mbar_wait_bounded(&bars[s], par));
         if (!ok) break;
-        const float *sb = buf + s * 9 * SEG;
-        const float *em = ring + (k % rslots) * SEG;          // eps row y-1
-        const float *e0r = ring + ((k + 1) % rslots) * SEG;   // eps row y
-        const float *ep = ring + ((k + 2) % rslots) * SEG;    // eps row y+1
-        const int y = r0 + k;
+        const float *sb = buf + s * Q * SEG;
+        const float *ey_slot[3] = {ring + (k % rslots) * (NZR * SEG),          // y-1
+                                   ring + ((k + 1) % rslots) * (NZR * SEG),    // y
+                                   ring + ((k + 2) % rslots) * (NZR * SEG)};   // y+1
+        const int y = y0 + k;
         const Nb3 Y = nb3<true>(y, d.ny, d.wall_y);
-        const long long ro = (long long)y * d.pitch + VANS_OFF;
+        const long long ro = row_offset(d, y, z);
 #pragma unroll
         for (int cc = 0; cc < CPT; ++cc) {
             const int xl = tid + cc * NT;
             const int x = xs + xl;
-            float h[9], et[9], o[9];
+            float h[Q], et[Q], o[Q];
 #pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                const bool bb = Y.wall[1 - L::ey(i)];
+            for (int i = 0; i < Q; ++i) {
+                const bool bb = Y.wall[1 - L::ey(i)] || Z.wall[1 - L::ez(i)];
                 h[i] = sb[i * SEG + 4 + xl + (bb ? 0 : -L::ex(i))];
             }
-            const float e0 = e0r[4 + xl];
-#pragma unroll
-            for (int i = 1; i < 9; ++i) {
-                const int ey = L::ey(i);
-                const float *er = ey > 0 ? ep : (ey < 0 ? em : e0r);
-                et[i] = Y.wall[1 + ey] ? e0 : er[4 + xl + L::ex(i)];
-            }
+            const float e0 = ey_slot[1][(Q == 9 ? 0 : 1) * SEG + 4 + xl];
             et[0] = e0;
-            collide<9>(d, h, e0, et, o);
+#pragma unroll
+            for (int i = 1; i < Q; ++i) {
+                const int ey = L::ey(i), ez = L::ez(i);
+                const bool wall = Y.wall[1 + ey] || Z.wall[1 + ez];
+                et[i] = wall ? e0 : ey_slot[1 + ey][(Q == 9 ? 0 : 1 + ez) * SEG + 4 + xl + L::ex(i)];
+            }
+            collide<Q>(d, h, e0, et, o);
             if (x < d.nx) {
 #pragma unroll
-                for (int i = 0; i < 9; ++i) fout[i * d.plane + ro + x] = o[i];
+                for (int i = 0; i < Q; ++i) fout[i * d.plane + ro + x] = o[i];
                 if (x == 0) {
 #pragma unroll
-                    for (int i = 0; i < 9; ++i)
+                    for (int i = 0; i < Q; ++i)
                         if (L::ex(i) < 0) fout[i * d.plane + ro + d.nx] = o[i];
                 }
                 if (x == d.nx - 1) {
 #pragma unroll
-                    for (int i = 0; i < 9; ++i)
+                    for (int i = 0; i < Q; ++i)
                         if (L::ex(i) > 0) fout[i * d.plane + ro - 1] = o[i];
                 }
             }
@@ -298,8 +321,8 @@ __global__ void __launch_bounds__(NT) k_step_tma_ring(const VDom d, const float 
         __syncthreads();
         if (tid == 0 && k + stages < n) {
             fence_proxy_async_smem();
-            issue_tile_ring<TW>(d, fin, r0 + k + stages, xs, k + stages, r0, buf + s * 9 * SEG, ring,
-                                rslots, &bars[s]);
+            issue_tile_ring<Q, TW>(d, fin, y0 + k + stages, z, xs, k + stages, y0, buf + s * Q * SEG,
+                                   ring, rslots, &bars[s]);
         }
         if (++s == stages) { s = 0; par ^= 1u; }
     }
@@ -314,13 +337,34 @@ __global__ void __launch_bounds__(NT) k_step_tma_ring(const VDom d, const float 
     }
 }
 
-template <int NT, int CPT>
+// Strips per (column block, plane): the smallest count whose grid fills the
+// resident CTA slots to >= 95 % in its last wave, else the best fill found.
+static int pick_per_y(int ncol, int ny, long long resident) {
+    int best = 1;
+    double best_eff = 0.0;
+    for (int p = 1; p <= ny; ++p) {
+        const long long grid = (long long)ncol * p;
+        const long long waves = (grid + resident - 1) / resident;
+        const double eff = (double)grid / (double)(waves * resident);
+        if (eff >= 0.95) return p;
+        if (eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best = p;
+        }
+        if (grid > 64 * resident) break;
+    }
+    return best;
+}
+
+template <int Q, int NT, int CPT>
 static cudaError_t launch_ring_t(const VDom &d, const float *fin, float *fout, int stages,
                                  cudaStream_t stream) {
     constexpr int TW = NT * CPT;
-    const size_t smem = kBarBytes + (size_t)(stages * 9 + stages + 2) * (TW + 8) * sizeof(float);
+    constexpr int NZR = (Q == 9) ? 1 : 3;
+    const size_t smem =
+        kBarBytes + (size_t)(stages * Q + (stages + 2) * NZR) * (TW + 8) * sizeof(float);
     if (stages < 2 || stages > 16 || smem > 227 * 1024) return cudaErrorInvalidValue;
-    auto kern = k_step_tma_ring<NT, CPT>;
+    auto kern = k_step_tma_ring<Q, NT, CPT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, occ = 0;
@@ -330,13 +374,11 @@ static cudaError_t launch_ring_t(const VDom &d, const float *fin, float *fout, i
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     const int ntx = (d.nx + TW - 1) / TW;
-    // strips per column block: fill the machine, at most one row per strip
-    int per_col = (sms * occ) / ntx;
-    if (per_col < 1) per_col = 1;
-    if (per_col > d.ny) per_col = d.ny;
-    const long long grid = (long long)per_col * ntx;
+    const int ncol = ntx * d.nz;
+    const int per_y = pick_per_y(ncol, d.ny, (long long)sms * occ);
+    const long long grid = (long long)ncol * per_y;
     if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    kern<<<(unsigned)grid, NT, smem, stream>>>(d, fin, fout, ntx, per_col, stages);
+    kern<<<(unsigned)grid, NT, smem, stream>>>(d, fin, fout, ntx, per_y, stages);
     return cudaGetLastError();
 }
 
@@ -377,11 +419,17 @@ cudaError_t launch_step_tma(int q, const VDom &d, const float *fin, float *fout,
                             cudaStream_t stream) {
     const int nt = 32 * L.warps;
     if (L.kind == 2) {
-        if (q != 9) return cudaErrorInvalidValue;
-        if (nt == 128 && L.cpt == 2) return launch_ring_t<128, 2>(d, fin, fout, L.rows, stream);
-        if (nt == 128 && L.cpt == 4) return launch_ring_t<128, 4>(d, fin, fout, L.rows, stream);
-        if (nt == 256 && L.cpt == 1) return launch_ring_t<256, 1>(d, fin, fout, L.rows, stream);
-        if (nt == 256 && L.cpt == 2) return launch_ring_t<256, 2>(d, fin, fout, L.rows, stream);
+#define VANS_RING_CASE(QQ, NTT, CC)                              \
+        if (q == QQ && nt == NTT && L.cpt == CC)                 \
+            return launch_ring_t<QQ, NTT, CC>(d, fin, fout, L.rows, stream);
+        VANS_RING_CASE(9, 128, 2)
+        VANS_RING_CASE(9, 128, 4)
+        VANS_RING_CASE(9, 256, 1)
+        VANS_RING_CASE(9, 256, 2)
+        VANS_RING_CASE(19, 128, 1)
+        VANS_RING_CASE(19, 128, 2)
+        VANS_RING_CASE(19, 256, 1)
+#undef VANS_RING_CASE
         return cudaErrorInvalidValue;
     }
 #define VANS_TMA_CASE(QQ, NTT, CC)                              \

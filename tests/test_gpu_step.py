@@ -31,10 +31,11 @@ STEP_CASES = [
     (9, (1, 7, 1100), 0, [Launch(2, 4, 3, 1), Launch(4, 4, 3, 1), Launch(2, 4, 4, 2)]),
     (9, (1, 40, 700), 2, [Launch(2, 8, 3, 2), Launch(1, 8, 5, 2)]),
     (19, (7, 9, 21), 6, [Launch(1, 2, 1), Launch(2, 2, 2), Launch(4, 1, 2), Launch(1, 4, 3, 1),
-                         Launch(2, 4, 2, 1)]),
-    (19, (5, 4, 33), 2, [Launch(2, 2, 1), Launch(1, 8, 3, 1)]),
-    (19, (3, 3, 4), 0, [Launch(1, 2, 1), Launch(1, 4, 4, 1)]),
-    (19, (1, 1, 2), 6, [Launch(1, 2, 1), Launch(1, 4, 3, 1)]),
+                         Launch(2, 4, 2, 1), Launch(1, 4, 3, 2), Launch(2, 4, 2, 2)]),
+    (19, (5, 4, 33), 2, [Launch(2, 2, 1), Launch(1, 8, 3, 1), Launch(1, 8, 2, 2)]),
+    (19, (3, 3, 4), 0, [Launch(1, 2, 1), Launch(1, 4, 4, 1), Launch(1, 4, 4, 2)]),
+    (19, (1, 1, 2), 6, [Launch(1, 2, 1), Launch(1, 4, 3, 1), Launch(1, 4, 3, 2)]),
+    (19, (6, 30, 300), 4, [Launch(2, 4, 3, 2), Launch(1, 8, 3, 2)]),
 ]
 
 
