@@ -40,18 +40,25 @@ WORKLOAD = ("D2Q9 4096x4096 periodic, eps smoothed noise (sigma 16) in [0.4,1.0]
 BYTES_PER_CELL = {9: 9 * 4 * 2 + 4, 19: 19 * 4 * 2 + 4}     # algorithmic bytes per update
 FALLBACK_HBM_GBS = 6800.0
 
-# DRAM bytes per launch of the D2Q9 step kernel measured by ncu
-# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by a hash of the kernel
-# sources they were taken on; a changed kernel reports null.
-TRAFFIC = {}
+# DRAM bytes per launch of the step kernel measured by ncu on the 4096^2
+# workload (dram__bytes_read.sum + dram__bytes_write.sum), keyed by launch shape
+# (cpt, warps, rows, kind) and a hash of the kernel sources they were taken on;
+# a changed kernel or another shape reports null.
+TRAFFIC = {
+    (4, 4, 3, 2, "5f2888d380b2edf6"): 681548288 + 553119744,   # profiles/step_d2q9_ring_4096_full.md
+}
+KERNEL_SOURCES = ("vans_step.cu", "vans_step_tma.cu", "vans_device.cuh", "vans_tma.cuh")
 
 
 def kernel_hash() -> str:
     h = hashlib.sha256()
-    for f in ("vans_step.cu", "vans_device.cuh"):
+    for f in KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_1406_6438_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+KERNEL_NAMES = {0: "k_step<9,cpt>", 1: "k_step_tma<9,32*warps,cpt>", 2: "k_step_tma_ring<9,32*warps,cpt>"}
 
 
 def peaks():
@@ -338,7 +345,8 @@ def main():
     per_launch = t / args.steps
     peak, peak_kind = peaks()
     achieved = BYTES_PER_CELL[9] * cells / per_launch / 1e9
-    traffic = TRAFFIC.get(kernel_hash()) if args.n == 4096 else None
+    key = (L.cpt, L.warps, L.rows, L.kind, kernel_hash())
+    traffic = TRAFFIC.get(key) if args.n == 4096 else None
 
     # end to end through the public API with host buffers: upload eps from
     # pinned host memory, set_eps, K steps, moments, copy rho and u back
@@ -400,7 +408,7 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": peak_kind, "bytes_per_cell": BYTES_PER_CELL[9],
-                     "kernel": "k_step<9,cpt>", "launch_us": per_launch * 1e6},
+                     "kernel": KERNEL_NAMES.get(L.kind, "?"), "launch_us": per_launch * 1e6},
         "e2e": {"value": world * cells * args.steps / t_e2e / 1e6, "unit": "MLUPS",
                 "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                 "note": "per K-step job: eps H2D, set_eps, K steps, moments, rho+u D2H"},
