@@ -83,7 +83,8 @@ typedef struct {
  * kind 2: the kind-1 pipeline where each CTA walks a strip of consecutive rows
  *         (one column block, one z plane) and keeps the porosity rows in a
  *         shared-memory ring, so each eps row is read from HBM once per strip.
- *         Kinds 1 and 2 are not available to the batched path. */
+ *         The batched path takes kinds 0 and 2 (kind 2: one CTA per strip of
+ *         up to 32 rows of one domain). */
 typedef struct {
     int cpt;
     int warps;

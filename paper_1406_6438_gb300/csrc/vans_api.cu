@@ -7,6 +7,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -103,7 +104,7 @@ bool launch_ok(const vans_launch *c, int q, bool batched) {
         if (c->warps < 1 || c->warps > 8 || c->rows < 1 || c->rows > 8) return false;
         return c->warps * c->rows <= 8;
     }
-    if ((c->kind != 1 && c->kind != 2) || batched) return false;
+    if ((c->kind != 1 && c->kind != 2) || (batched && c->kind != 2)) return false;
     if (c->rows < 2 || c->rows > 6) return false;
     // the instantiated pipeline shapes
     const int nt = 32 * c->warps;
@@ -169,6 +170,8 @@ void drop_graph(vans_t h) {
 
 cudaError_t one_step(vans_t h, cudaStream_t s, int par) {
     ++h->launches;
+    if (h->batched && h->L.kind == 2)
+        return vans::launch_ring_batched(h->doms_d, h->tiles_d, (int)h->tiles.size(), par, h->L, s);
     if (h->batched)
         return vans::launch_step_batched(h->doms_d, h->tiles_d, (int)h->tiles.size(), par, h->L,
                                          h->grid, s);
@@ -245,9 +248,30 @@ int read_flag(vans_t h, int *value, int *timeout = nullptr) {
     return VANS_OK;
 }
 
+constexpr int kStripRows = 32;   // rows per strip of the batched pipeline kernel
+
 void build_tiles(vans_t h, const Launch &L, std::vector<Tile> &out) {
     out.clear();
     const int bx = 32 * L.cpt * L.warps;
+    if (L.kind == 2) {
+        // strips of up to kStripRows rows per column block, largest first so the
+        // last wave of CTAs holds the short ones
+        for (int d = 0; d < h->n; ++d) {
+            const VDom &D = h->doms[d];
+            const int per_y = (D.ny + kStripRows - 1) / kStripRows;
+            for (int yc = 0; yc < per_y; ++yc) {
+                const int y0 = (int)((long long)yc * D.ny / per_y);
+                const int y1 = (int)((long long)(yc + 1) * D.ny / per_y);
+                for (int x = 0; x < D.nx; x += bx) out.push_back(Tile{d, y0, x, y1});
+            }
+        }
+        std::stable_sort(out.begin(), out.end(), [&](const Tile &a, const Tile &b) {
+            const long long wa = (long long)(a.pad - a.row) * std::min(bx, h->doms[a.dom].nx - a.x0);
+            const long long wb = (long long)(b.pad - b.row) * std::min(bx, h->doms[b.dom].nx - b.x0);
+            return wa > wb;
+        });
+        return;
+    }
     for (int d = 0; d < h->n; ++d) {
         const VDom &D = h->doms[d];
         for (int r = 0; r < D.rows; r += L.rows)
@@ -300,7 +324,12 @@ std::vector<Launch> candidates(int q, bool batched) {
                 if (q == 19 && cpt == 4 && warps * rows > 4) continue;
                 c.push_back(Launch{cpt, warps, rows, 0});
             }
-    if (batched) return c;
+    if (batched) {
+        const Launch t[] = {{2, 4, 3, 2}, {4, 4, 2, 2}, {4, 4, 3, 2}, {2, 8, 2, 2}, {2, 8, 3, 2},
+                            {1, 8, 3, 2}};
+        c.insert(c.end(), t, t + 6);
+        return c;
+    }
     // bulk-copy pipeline shapes {cpt, warps, stages, 1}
     if (q == 9) {
         const Launch t[] = {{2, 4, 3, 1}, {2, 4, 4, 1}, {4, 4, 2, 1}, {4, 4, 3, 1},
@@ -691,6 +720,7 @@ int vans_batch_create(const vans_params *p, int n, void *workspace, size_t works
         w += (2 * sf + eps_floats_of(p[d].nx, p[d].ny, 1)) * sizeof(float);
     }
     h->flag = (int *)w;
+    for (VDom &D : h->doms) D.status = h->flag + 1;
     h->dom_ready.assign(n, 0);
     int rc = make_streams(h, cuda_stream);
     if (rc) {

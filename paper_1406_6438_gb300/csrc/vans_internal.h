@@ -30,12 +30,14 @@ struct VDom {
     int *status;          // device status word: bit 1 = a bounded wait timed out
 };
 
-// One tile of the batched kernel: a block-sized piece of one domain.
+// One tile of the batched register-load kernel: a block-sized piece of one
+// domain.  The batched pipeline kernel reuses the record as a strip:
+// {dom, y0, x0, y1} = rows y0..y1-1 of the column block at x0.
 struct Tile {
     int dom;   // domain index
-    int row;   // first row of the tile
+    int row;   // first row of the tile (strip: first row)
     int x0;    // first column of the tile
-    int pad;
+    int pad;   // strip: one past the last row
 };
 
 // kind 0: register-load kernel k_step (cpt cells per lane, warps x rows per block)
@@ -52,6 +54,8 @@ cudaError_t launch_step(int q, const VDom &d, const float *fin, float *fout, Lau
                         cudaStream_t stream);
 cudaError_t launch_step_tma(int q, const VDom &d, const float *fin, float *fout, Launch L,
                             cudaStream_t stream);
+cudaError_t launch_ring_batched(const VDom *doms, const Tile *strips, int nstrips, int parity,
+                                Launch L, cudaStream_t stream);
 cudaError_t launch_step_batched(const VDom *doms_dev, const Tile *tiles_dev, int ntiles, int parity,
                                 Launch L, int grid, cudaStream_t stream);
 int batched_blocks_per_sm(Launch L);

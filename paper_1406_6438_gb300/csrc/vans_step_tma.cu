@@ -228,30 +228,22 @@ __device__ __forceinline__ void issue_tile_ring(const VDom &d, const float *__re
     }
 }
 
+// One strip of tiles: column block starting at xs, plane z, rows [y0, y1).
 template <int Q, int NT, int CPT>
-__global__ void __launch_bounds__(NT) k_step_tma_ring(const VDom d, const float *__restrict__ fin,
-                                                      float *__restrict__ fout, int ntx, int per_y,
-                                                      int stages) {
+__device__ __forceinline__ void ring_strip(const VDom &d, const float *__restrict__ fin,
+                                           float *__restrict__ fout, int xs, int z, int y0, int y1,
+                                           int stages, unsigned char *smem) {
     using L = Lat<Q>;
     constexpr int TW = NT * CPT;
     constexpr int SEG = TW + 8;
     constexpr int NZR = (Q == 9) ? 1 : 3;
-    extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
     float *buf = reinterpret_cast<float *>(smem + kBarBytes);
     float *ring = buf + stages * Q * SEG;
     const int rslots = stages + 2;
     const int tid = threadIdx.x;
-    // strip of this CTA: column block xt, plane z, rows [y0, y1)
-    const int xt = blockIdx.x % ntx;
-    const int rem = blockIdx.x / ntx;
-    const int z = rem % d.nz;
-    const int yc = rem / d.nz;
-    const int y0 = (int)((long long)yc * d.ny / per_y);
-    const int y1 = (int)((long long)(yc + 1) * d.ny / per_y);
     const int n = y1 - y0;
     if (n <= 0) return;
-    const int xs = xt * TW;
 
     if (tid == 0) {
         for (int s = 0; s < stages; ++s) mbar_init(&bars[s], 1);
@@ -337,6 +329,36 @@ __global__ void __launch_bounds__(NT) k_step_tma_ring(const VDom d, const float 
     }
 }
 
+template <int Q, int NT, int CPT>
+__global__ void __launch_bounds__(NT) k_step_tma_ring(const VDom d, const float *__restrict__ fin,
+                                                      float *__restrict__ fout, int ntx, int per_y,
+                                                      int stages) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    // strip of this CTA: column block xt, plane z, rows [y0, y1)
+    const int xt = blockIdx.x % ntx;
+    const int rem = blockIdx.x / ntx;
+    const int z = rem % d.nz;
+    const int yc = rem / d.nz;
+    const int y0 = (int)((long long)yc * d.ny / per_y);
+    const int y1 = (int)((long long)(yc + 1) * d.ny / per_y);
+    ring_strip<Q, NT, CPT>(d, fin, fout, xt * NT * CPT, z, y0, y1, stages, smem);
+}
+
+// Batched D2Q9: CTA b takes strip b of a table built on the host (domain,
+// column block, rows y0..y1-1; largest strips first) and advances it with the
+// porosity-ring pipeline, using that domain's descriptor and buffers.
+template <int NT, int CPT>
+__global__ void __launch_bounds__(NT) k_step_ring_batched(const VDom *__restrict__ doms,
+                                                          const Tile *__restrict__ strips, int parity,
+                                                          int stages) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const Tile S = strips[blockIdx.x];   // {dom, y0, x0, y1}
+    const VDom d = doms[S.dom];
+    const float *fin = parity ? d.f[1] : d.f[0];
+    float *fout = parity ? d.f[0] : d.f[1];
+    ring_strip<9, NT, CPT>(d, fin, fout, S.x0, 0, S.row, S.pad, stages, smem);
+}
+
 // Strips per (column block, plane): the smallest count whose grid fills the
 // resident CTA slots to >= 95 % in its last wave, else the best fill found.
 static int pick_per_y(int ncol, int ny, long long resident) {
@@ -411,6 +433,29 @@ static cudaError_t launch_tma_t(const VDom &d, const float *fin, float *fout, in
     if (grid > ntiles) grid = ntiles;
     kern<<<(unsigned)grid, NT, smem, stream>>>(d, fin, fout, ntx, (int)ntiles, stages);
     return cudaGetLastError();
+}
+
+template <int NT, int CPT>
+static cudaError_t launch_ring_batched_t(const VDom *doms, const Tile *strips, int nstrips, int parity,
+                                         int stages, cudaStream_t stream) {
+    constexpr int TW = NT * CPT;
+    const size_t smem = kBarBytes + (size_t)(stages * 9 + (stages + 2)) * (TW + 8) * sizeof(float);
+    if (stages < 2 || stages > 16 || smem > 227 * 1024 || nstrips < 1) return cudaErrorInvalidValue;
+    auto kern = k_step_ring_batched<NT, CPT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<nstrips, NT, smem, stream>>>(doms, strips, parity, stages);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ring_batched(const VDom *doms, const Tile *strips, int nstrips, int parity,
+                                Launch L, cudaStream_t stream) {
+    const int nt = 32 * L.warps;
+    if (nt == 128 && L.cpt == 2) return launch_ring_batched_t<128, 2>(doms, strips, nstrips, parity, L.rows, stream);
+    if (nt == 128 && L.cpt == 4) return launch_ring_batched_t<128, 4>(doms, strips, nstrips, parity, L.rows, stream);
+    if (nt == 256 && L.cpt == 1) return launch_ring_batched_t<256, 1>(doms, strips, nstrips, parity, L.rows, stream);
+    if (nt == 256 && L.cpt == 2) return launch_ring_batched_t<256, 2>(doms, strips, nstrips, parity, L.rows, stream);
+    return cudaErrorInvalidValue;
 }
 
 // L.warps -> threads per CTA (32 * warps), L.cpt -> cells per thread per tile,

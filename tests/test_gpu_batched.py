@@ -38,7 +38,8 @@ def test_batched_matches_oracle_per_domain():
         assert np.abs(rho.cpu().numpy() - rho_o).max() <= 1e-5, d
 
 
-@pytest.mark.parametrize("L", [Launch(1, 2, 1), Launch(2, 1, 2), Launch(4, 4, 1), Launch(4, 2, 2)])
+@pytest.mark.parametrize("L", [Launch(1, 2, 1), Launch(2, 1, 2), Launch(4, 4, 1), Launch(4, 2, 2),
+                               Launch(4, 4, 3, 2), Launch(2, 8, 2, 2), Launch(1, 8, 3, 2)])
 def test_batched_launch_shapes(L):
     torch = torch_cuda()
     doms = W.batched_channels(n=4, seed=43, nx_range=(20, 300), ny_range=(4, 40))
@@ -52,18 +53,19 @@ def test_batched_launch_shapes(L):
         assert np.abs(f - f_o).max() <= 5e-7, (L, d)
 
 
-def test_batched_equals_single_domain_solver():
-    """The batched kernel and the single-domain kernel run the same per-cell
+@pytest.mark.parametrize("L", [Launch(4, 4, 1), Launch(4, 4, 3, 2)])
+def test_batched_equals_single_domain_solver(L):
+    """The batched kernels and the single-domain kernels run the same per-cell
     arithmetic: identical populations after a graph-replayed run."""
     torch = torch_cuda()
     import paper_1406_6438_gb300 as V
-    doms = W.batched_channels(n=3, seed=44, nx_range=(60, 200), ny_range=(20, 70))
+    doms = W.batched_channels(n=3, seed=44, nx_range=(60, 700), ny_range=(20, 90))
     b = _batch(doms)
-    b.launch = Launch(4, 4, 1)
+    b.launch = L
     b.step(130)
     for d, (p, eps) in enumerate(doms):
         s = V.Solver(p)
         s.set_eps(torch.from_numpy(eps).cuda().view(-1))
-        s.launch = Launch(4, 4, 1)
+        s.launch = L
         s.step(130)
         assert torch.equal(s.populations(), b.populations(d))
