@@ -207,6 +207,23 @@ def reference_arm(args):
     return 0
 
 
+# ------------------------------------------------------------- ranks -------
+def max_over_ranks(value: float, dist, device) -> float:
+    """The largest value over all ranks (each rank's timed region; the job is
+    as slow as its slowest replica).  Without a process group: the value."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(world: int, cells: int, steps: int, seconds: float) -> float:
+    """Whole-job lattice updates per second over all replicas, in millions."""
+    return world * cells * steps / seconds / 1e6
+
+
 # --------------------------------------------------------------- GPU arm ---
 def time_region(torch, stream, fn):
     a = torch.cuda.Event(enable_timing=True)
@@ -336,12 +353,9 @@ def main():
     with ClockSampler(gpu_uuid(torch, local)) as clk:
         t = time_region(torch, sim.stream, lambda: sim.step(args.steps))
     launches = sim.launch_count - c0
-    if dist:
-        tt = torch.tensor([t], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = tt.item()
+    t = max_over_ranks(t, dist, "cuda")
     ok = sim.check()
-    value = world * cells * args.steps / t / 1e6
+    value = job_mlups(world, cells, args.steps, t)
     per_launch = t / args.steps
     peak, peak_kind = peaks()
     achieved = BYTES_PER_CELL[9] * cells / per_launch / 1e9
@@ -367,10 +381,7 @@ def main():
 
     with torch.cuda.stream(sim.stream):
         t_e2e = time_region(torch, sim.stream, e2e)
-    if dist:
-        tt = torch.tensor([t_e2e], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_e2e = tt.item()
+    t_e2e = max_over_ranks(t_e2e, dist, "cuda")
     h2d = cells * 4
     d2h = 3 * cells * 4
     sim.close()
@@ -409,7 +420,7 @@ def main():
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": peak_kind, "bytes_per_cell": BYTES_PER_CELL[9],
                      "kernel": KERNEL_NAMES.get(L.kind, "?"), "launch_us": per_launch * 1e6},
-        "e2e": {"value": world * cells * args.steps / t_e2e / 1e6, "unit": "MLUPS",
+        "e2e": {"value": job_mlups(world, cells, args.steps, t_e2e), "unit": "MLUPS",
                 "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                 "note": "per K-step job: eps H2D, set_eps, K steps, moments, rho+u D2H"},
         "gpu_launches": launches,

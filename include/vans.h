@@ -72,6 +72,11 @@ typedef struct {
     float d_p;      /* particle diameter (k_mode 0)                                  */
     float K;        /* permeability (k_mode 1, 2)                                    */
     float F_eps;    /* geometric function (k_mode 1)                                 */
+    float u_wall[3];/* velocity of the upper y wall (y = ny side), the plate that drives
+                       the Couette flow of the validation case; needs y walls.  A
+                       population that bounces off it gains 2 w_i eps rho_w (e_i.u_w)/cs^2
+                       with rho_w = 1 (moving-wall bounce-back with the eps-weighted
+                       equilibrium of Eq. d2q9eq).  All zero: resting walls.         */
 } vans_params;
 
 /* Launch configuration of the step kernels (chosen by vans_autotune).
@@ -117,7 +122,8 @@ void vans_destroy(vans_t h);
 
 /* Copy the porosity field eps (dense, nx*ny*nz floats, device) into the
  * workspace and reset the populations to rest, rho = 1 and u = 0, i.e.
- * f_i = w_i eps (the initial state of the validation case).  Every eps must
+ * f_i = w_i eps (the initial state of the validation case), also next to a
+ * moving upper wall.  Every eps must
  * satisfy 0 < eps <= 1; otherwise VANS_ERR_ARG and the handle keeps its
  * previous state.  (Synchronises the stream once to check the range.) */
 int vans_set_eps(vans_t h, const float *eps_dev);
@@ -224,7 +230,8 @@ long long vans_batch_cells(vans_t h);
 /* ------------------------------------------------- no-allocation step --- */
 
 /* One step from state_in to state_out (vans_state_floats(p) floats each,
- * distinct buffers; an all-zero buffer is the rest state f = w eps) for a
+ * distinct buffers; without a moving wall an all-zero buffer is the rest
+ * state f = w eps) for a
  * caller that cannot allocate device memory or hand the library a workspace:
  * code that runs inside another framework's memory pool or allocator, code that
  * may not call cudaMalloc while a CUDA graph is being captured, or an embedded

@@ -263,7 +263,7 @@ static void grad_eps_field(const or_params *p, const lattice_t *L, const double 
     const int nx = p->nx, ny = p->ny, nz = p->nz;
     const long N = (long)nx * ny * nz;
     const int wx = p->wall_mask & 1, wy = (p->wall_mask >> 1) & 1, wz = (p->wall_mask >> 2) & 1;
-#pragma omp parallel for collapse(2) schedule(static)
+#pragma omp parallel for collapse(2) schedule(static) if ((long)nx * ny * nz > 8192)
     for (int z = 0; z < nz; ++z)
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {
@@ -363,7 +363,7 @@ int or_moments(const or_params *p, const double *eps, const double *f, double *r
     double *grad = (double *)malloc(sizeof(double) * 3 * N);
     if (!grad) return -2;
     grad_eps_field(p, &L, eps, grad);
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (N > 8192)
     for (long n = 0; n < N; ++n) {
         double fc[19], gc[3] = {grad[n], grad[N + n], grad[2 * N + n]};
         cell_t c;
@@ -382,7 +382,7 @@ static void collide(const or_params *p, const lattice_t *L, const double *eps, c
 {
     const long N = (long)p->nx * p->ny * p->nz;
     const double tau = p->tau;
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (N > 8192)
     for (long n = 0; n < N; ++n) {
         double fc[19], feq[19], S[19], gc[3] = {grad[n], grad[N + n], grad[2 * N + n]};
         cell_t c;
@@ -405,7 +405,7 @@ static void stream(const or_params *p, const lattice_t *L, const double *eps, co
     const int nx = p->nx, ny = p->ny, nz = p->nz;
     const long N = (long)nx * ny * nz;
     const int wx = p->wall_mask & 1, wy = (p->wall_mask >> 1) & 1, wz = (p->wall_mask >> 2) & 1;
-#pragma omp parallel for collapse(2) schedule(static)
+#pragma omp parallel for collapse(2) schedule(static) if ((long)nx * ny * nz > 8192)
     for (int z = 0; z < nz; ++z)
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {

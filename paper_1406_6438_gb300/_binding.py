@@ -32,7 +32,7 @@ class _CParams(ctypes.Structure):
         ("q", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
         ("wall_mask", ctypes.c_int), ("tau", ctypes.c_float), ("g", ctypes.c_float * 3),
         ("drag_mode", ctypes.c_int), ("k_mode", ctypes.c_int), ("d_p", ctypes.c_float),
-        ("K", ctypes.c_float), ("F_eps", ctypes.c_float),
+        ("K", ctypes.c_float), ("F_eps", ctypes.c_float), ("u_wall", ctypes.c_float * 3),
     ]
 
 
@@ -56,6 +56,7 @@ class Params:
     d_p: float = 1.0
     K: float = 1.0
     F_eps: float = 0.0
+    u_wall: tuple = (0.0, 0.0, 0.0)
 
     @classmethod
     def of(cls, p) -> "Params":
@@ -63,9 +64,11 @@ class Params:
 
     def c(self) -> _CParams:
         g = tuple(float(v) for v in self.g) + (0.0,) * (3 - len(self.g))
+        uw = tuple(float(v) for v in self.u_wall) + (0.0,) * (3 - len(self.u_wall))
         return _CParams(int(self.q), int(self.nx), int(self.ny), int(self.nz), int(self.wall_mask),
                         float(self.tau), (ctypes.c_float * 3)(*g), int(self.drag_mode),
-                        int(self.k_mode), float(self.d_p), float(self.K), float(self.F_eps))
+                        int(self.k_mode), float(self.d_p), float(self.K), float(self.F_eps),
+                        (ctypes.c_float * 3)(*uw))
 
     @property
     def dim(self) -> int:

@@ -49,7 +49,9 @@ int validate(const vans_params *p, bool batched) {
     if (p->q == 9 && (p->wall_mask & 4)) return VANS_ERR_ARG;
     if (!(p->tau > 0.5f) || !isfinite(p->tau)) return VANS_ERR_ARG;
     for (int k = 0; k < 3; ++k)
-        if (!isfinite(p->g[k])) return VANS_ERR_ARG;
+        if (!isfinite(p->g[k]) || !isfinite(p->u_wall[k])) return VANS_ERR_ARG;
+    const bool moving = p->u_wall[0] != 0.f || p->u_wall[1] != 0.f || p->u_wall[2] != 0.f;
+    if (moving && !(p->wall_mask & 2)) return VANS_ERR_ARG;     // the plate is a y wall
     if (p->drag_mode < 0 || p->drag_mode > 2) return VANS_ERR_ARG;
     if (p->k_mode < 0 || p->k_mode > 2) return VANS_ERR_ARG;
     if (p->drag_mode != 0) {
@@ -95,6 +97,10 @@ void fill_dom(const vans_params *p, VDom &d) {
         d.cb = (float)(1.75 / sqrt(150.0 * p->K));
     }
     d.cells = (long long)p->nx * p->ny * p->nz;
+    d.uw[0] = p->u_wall[0];
+    d.uw[1] = p->u_wall[1];
+    d.uw[2] = (p->q == 19) ? p->u_wall[2] : 0.f;
+    d.moving = (d.uw[0] != 0.f || d.uw[1] != 0.f || d.uw[2] != 0.f) ? 1 : 0;
 }
 
 bool launch_ok(const vans_launch *c, int q, bool batched) {
@@ -421,6 +427,11 @@ int vans_set_eps(vans_t h, const float *eps_dev) {
         return VANS_ERR_CUDA;
     if (cudaMemsetAsync(h->st[0], 0, 2 * h->sfloats * sizeof(float), h->stream) != cudaSuccess)
         return VANS_ERR_CUDA;
+    if (h->dom.moving) {
+        ++h->launches;
+        if (vans::launch_init_moving(h->q, h->dom, h->st[0], h->stream) != cudaSuccess)
+            return VANS_ERR_CUDA;
+    }
     h->cur = 0;
     h->eps_set = true;
     return VANS_OK;
@@ -759,6 +770,11 @@ int vans_batch_set_eps(vans_t h, int d, const float *eps_dev) {
     const long long sf = state_floats_of(9, D.nx, D.ny, 1);
     if (cudaMemsetAsync(D.f[0], 0, 2 * sf * sizeof(float), h->stream) != cudaSuccess)
         return VANS_ERR_CUDA;
+    if (D.moving) {
+        ++h->launches;
+        if (vans::launch_init_moving(9, D, D.f[h->parity], h->stream) != cudaSuccess)
+            return VANS_ERR_CUDA;
+    }
     h->dom_ready[d] = 1;
     return VANS_OK;
 }

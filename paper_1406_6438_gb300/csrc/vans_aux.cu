@@ -73,6 +73,7 @@ __global__ void k_moments(const VDom d, const float *__restrict__ st, float *__r
         float h[Q], e0, et[Q];
         pull_cell<Q>(d, st, x, y, z, Y, Z, h);
         eps_cell<Q>(d, x, y, z, Y, Z, e0, et);
+        apply_moving_wall<Q>(d, Y.wall[2], Z, e0, h);
         Macro<Q> M;
         macro<Q>(d, h, e0, et, M);
         if (rho) rho[n] = M.rho;
@@ -94,9 +95,11 @@ __global__ void k_export(const VDom d, const float *__restrict__ st, float *__re
         Nb3 Y, Z;
         nb_yz<Q>(d, y, z, Y, Z);
         const float e0 = d.eps[row_offset(d, y, z) + x];
+        float h[Q];
+        pull_cell<Q>(d, st, x, y, z, Y, Z, h);
+        apply_moving_wall<Q>(d, Y.wall[2], Z, e0, h);
 #pragma unroll
-        for (int i = 0; i < Q; ++i)
-            f[i * d.cells + n] = st[pull_index<Q>(d, i, x, y, z, Y, Z)] + L::w(i) * e0;
+        for (int i = 0; i < Q; ++i) f[i * d.cells + n] = h[i] + L::w(i) * e0;
     }
 }
 
@@ -111,9 +114,35 @@ __global__ void k_import(const VDom d, const float *__restrict__ f, float *__res
         Nb3 Y, Z;
         nb_yz<Q>(d, y, z, Y, Z);
         const float e0 = d.eps[row_offset(d, y, z) + x];
+        const bool top = d.moving && Y.wall[2];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            float v = f[i * d.cells + n] - L::w(i) * e0;
+            if (top && L::ey(i) < 0 && !Z.wall[1 - L::ez(i)]) v -= wall_gain<Q>(d, i, e0);
+            st[pull_index<Q>(d, i, x, y, z, Y, Z)] = v;
+        }
+    }
+}
+
+// Rest state f = w eps with a moving upper wall: the all-zero deviation buffer
+// would pull w eps plus the wall gain in the top rows, so store minus the gain
+// in the entries those rows pull through the moving wall.
+template <int Q>
+__global__ void k_init_moving(const VDom d, float *__restrict__ st) {
+    using L = Lat<Q>;
+    const long long n_top = (long long)d.nx * d.nz;        // cells of the rows y = ny-1
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n_top;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(t % d.nx);
+        const int z = (int)(t / d.nx);
+        const int y = d.ny - 1;
+        Nb3 Y, Z;
+        nb_yz<Q>(d, y, z, Y, Z);
+        const float e0 = d.eps[row_offset(d, y, z) + x];
 #pragma unroll
         for (int i = 0; i < Q; ++i)
-            st[pull_index<Q>(d, i, x, y, z, Y, Z)] = f[i * d.cells + n] - L::w(i) * e0;
+            if (L::ey(i) < 0 && !Z.wall[1 - L::ez(i)])
+                st[pull_index<Q>(d, i, x, y, z, Y, Z)] = -wall_gain<Q>(d, i, e0);
     }
 }
 
@@ -153,6 +182,7 @@ __global__ void k_check(const VDom d, const float *__restrict__ st, int *flag) {
         float h[Q], e0, et[Q];
         pull_cell<Q>(d, st, x, y, z, Y, Z, h);
         eps_cell<Q>(d, x, y, z, Y, Z, e0, et);
+        apply_moving_wall<Q>(d, Y.wall[2], Z, e0, h);
         Macro<Q> M;
         macro<Q>(d, h, e0, et, M);
         if (!isfinite(M.R) || !isfinite(M.un) || !(M.un < 0.5f)) atomicOr(flag, 1);
@@ -185,6 +215,7 @@ __global__ void __launch_bounds__(256) k_flux(const VDom d, const float *__restr
         float h[Q], e0, et[Q];
         pull_cell<Q>(d, st, x_out, y, z, Y, Z, h);
         eps_cell<Q>(d, x_out, y, z, Y, Z, e0, et);
+        apply_moving_wall<Q>(d, Y.wall[2], Z, e0, h);
         Macro<Q> M;
         macro<Q>(d, h, e0, et, M);
         acc += M.R * M.u[0];
@@ -212,6 +243,7 @@ __global__ void k_flux_seed(const VDom d, const float *__restrict__ st, int x_ou
         float h[Q], e0, et[Q];
         pull_cell<Q>(d, st, x_out, y, z, Y, Z, h);
         eps_cell<Q>(d, x_out, y, z, Y, Z, e0, et);
+        apply_moving_wall<Q>(d, Y.wall[2], Z, e0, h);
         MacroT<Q, T> M;
         macro_t<Q, T>(d, h, e0, et, M);
         // J_cell = R u_x
@@ -304,8 +336,17 @@ __device__ __forceinline__ void adj_row(const VDom &d, const float *__restrict__
             const bool wall = Y.wall[1 + L::ey(i)] || Z.wall[1 + L::ez(i)];
             et[i] = (i == 0 || wall) ? e0 : E[1 + L::ey(i)][1 + L::ez(i)][k + 1 + L::ex(i)];
         }
+        if (EDGE) apply_moving_wall<Q>(d, Y.wall[2], Z, e0, hh);
         T ebar, gbar[3];
         collide_vjp_t<Q, T>(d, hh, e0, et, mm, ll, ebar, gbar);
+        if (EDGE && d.moving && Y.wall[2]) {
+            // the populations this cell sends into the moving wall come back
+            // as their opposites with a gain that is linear in eps(x)
+#pragma unroll
+            for (int i = 0; i < Q; ++i)
+                if (L::ey(i) > 0 && !Z.wall[1 + L::ez(i)])
+                    ebar += (T)wall_gain<Q>(d, L::opp(i), 1.f) * (T)mm[i];
+        }
 #pragma unroll
         for (int i = 0; i < Q; ++i) lam[i][k] = ll[i];
         if (x0 + k < d.nx) {
@@ -438,6 +479,14 @@ cudaError_t launch_pad_eps(const VDom &d, const float *eps_dense, float *eps_pad
                            cudaStream_t s) {
     const int g = grid_for((long long)d.rows * d.pitch, 256);
     k_pad_eps<<<g, 256, 0, s>>>(d, eps_dense, eps_pad, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_moving(int q, const VDom &d, float *state, cudaStream_t s) {
+    if (!d.moving || !d.wall_y) return cudaSuccess;
+    const int g = grid_for((long long)d.nx * d.nz, 256);
+    VANS_DISPATCH_Q(q, (k_init_moving<9><<<g, 256, 0, s>>>(d, state)),
+                    (k_init_moving<19><<<g, 256, 0, s>>>(d, state)));
     return cudaGetLastError();
 }
 

@@ -221,6 +221,32 @@ __device__ __forceinline__ long long row_offset(const VDom &d, int y, int z) {
     return ((long long)z * d.ny + y) * d.pitch + VANS_OFF;
 }
 
+// Moving upper wall: a population pulled through the upper y wall (direction
+// i with e_iy < 0 in a top row) left the cell as its opposite and bounced off
+// the moving plate, gaining 2 w_i eps (e_i . u_w)/cs^2 (rho_w = 1).  top is
+// true in the rows whose +y neighbour lies past that wall.  A population that
+// crossed a z wall at the same time (a D3Q19 edge direction in a corner row)
+// takes a plain bounce-back.
+template <int Q>
+__device__ __forceinline__ float wall_gain(const VDom &d, int i, float e0) {
+    using L = Lat<Q>;
+    float eu = 0.f;
+    if (L::ex(i)) eu += L::ex(i) * d.uw[0];
+    if (L::ey(i)) eu += L::ey(i) * d.uw[1];
+    if (Q == 19 && L::ez(i)) eu += L::ez(i) * d.uw[2];
+    return 6.f * L::w(i) * e0 * eu;
+}
+
+template <int Q>
+__device__ __forceinline__ void apply_moving_wall(const VDom &d, bool top, const Nb3 &Z, float e0,
+                                                  float h[Q]) {
+    using L = Lat<Q>;
+    if (!(d.moving && top)) return;
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+        if (L::ey(i) < 0 && !Z.wall[1 - L::ez(i)]) h[i] += wall_gain<Q>(d, i, e0);
+}
+
 // ----------------------------------------------------------- the drag ----
 // alpha = eps^2 nu / K and beta = eps^3 F_eps / sqrt(K) (drag law) with K and
 // F_eps per k_mode; ca, cb are the host-side constants of vans_internal.h.
@@ -260,6 +286,25 @@ __device__ __forceinline__ void drag(const VDom &d, float e, float inv_e, float 
     if (DERIV) { *dalpha = da; *dbeta = db; }
 }
 
+// --------------------------------------------------- reciprocal and root ----
+// The hardware estimates (MUFU rcp / rsqrt) carry a small input-dependent bias;
+// on a near-steady flow it acts the same way every step and accumulates.  One
+// Newton-Raphson step on each estimate (the textbook iteration r <- r (2 - x r)
+// for 1/x, s <- s + (x - s^2)/(2 s) for sqrt x) removes it for a few FMAs,
+// far cheaper than the correctly rounded library routines.
+__device__ __forceinline__ float rcp_nr(float x) {
+    const float r = __fdividef(1.f, x);
+    const float e = fmaf(-x, r, 1.f);
+    return fmaf(r, e, r);
+}
+
+__device__ __forceinline__ float sqrt_nr(float x) {     // x > 0
+    const float y = rsqrtf(x);
+    const float s = x * y;
+    const float e = fmaf(-s, s, x);
+    return fmaf(0.5f * y, e, s);
+}
+
 // ----------------------------------------------------- cell macroscopics ----
 // Moments of one cell (Eqs. 0moment and 1moment) from its pulled deviations
 // h_i = f_i - w_i eps(x) and the porosities eps~_i = eps(x + e_i).
@@ -290,7 +335,13 @@ __device__ __forceinline__ void macro(const VDom &d, const float h[Q], float e0,
     M.dl = dl;
     M.e0 = e0;
     M.R = e0 + dl;
+#if defined(VANS_IEEE_MATH)
+    M.inv_e = __frcp_rn(e0);
+#elif defined(VANS_RAW_ESTIMATES)
     M.inv_e = __fdividef(1.f, e0);
+#else
+    M.inv_e = rcp_nr(e0);
+#endif
     M.rho = M.R * M.inv_e;
     // grad eps = (1/cs^2) sum_i w_i e_i eps~_i and sum_i e_i f_i = sum_i e_i h_i,
     // both over opposite pairs: eps~_i - eps~_opp(i) is exact in FP32 for
@@ -322,11 +373,23 @@ __device__ __forceinline__ void macro(const VDom &d, const float h[Q], float e0,
     M.b = 0.5f * M.beta;
     // square roots and the reciprocal through the hardware approximations
     // (relative error ~1e-7, far below the FP32 rounding of the populations)
+#if defined(VANS_IEEE_MATH)
+    M.mm = sqrtf(mm2);
+    M.sq = sqrtf(M.a * M.a + 4.f * M.b * M.mm);
+    M.D = M.a + M.sq;
+    M.s = __fdiv_rn(2.f, M.D);
+#elif defined(VANS_RAW_ESTIMATES)
     M.mm = mm2 > 0.f ? mm2 * rsqrtf(mm2) : 0.f;
     const float q2 = M.a * M.a + 4.f * M.b * M.mm;
     M.sq = q2 * rsqrtf(q2);
     M.D = M.a + M.sq;
     M.s = __fdividef(2.f, M.D);
+#else
+    M.mm = mm2 > 0.f ? sqrt_nr(mm2) : 0.f;
+    M.sq = sqrt_nr(M.a * M.a + 4.f * M.b * M.mm);
+    M.D = M.a + M.sq;
+    M.s = 2.f * rcp_nr(M.D);
+#endif
     M.un = M.mm * M.s;
     const float kd = M.alpha + M.beta * M.un;
 #pragma unroll

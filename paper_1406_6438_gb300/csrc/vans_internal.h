@@ -28,6 +28,8 @@ struct VDom {
     long long cells;      // nx * ny * nz
     long long dense_off;  // offset of this domain in packed dense outputs (batched)
     int *status;          // device status word: bit 1 = a bounded wait timed out
+    int moving;           // 1: the upper y wall moves with velocity uw
+    float uw[3];
 };
 
 // One tile of the batched register-load kernel: a block-sized piece of one
@@ -65,6 +67,7 @@ cudaError_t launch_export(int q, const VDom &d, const float *state, float *f, cu
 cudaError_t launch_import(int q, const VDom &d, const float *f, float *state, cudaStream_t stream);
 cudaError_t launch_pad_eps(const VDom &d, const float *eps_dense, float *eps_pad, int *flag,
                            cudaStream_t stream);
+cudaError_t launch_init_moving(int q, const VDom &d, float *state, cudaStream_t stream);
 cudaError_t launch_check(int q, const VDom &d, const float *state, int *flag, cudaStream_t stream);
 cudaError_t launch_flux(int q, const VDom &d, const float *state, int x_out, float *J,
                         cudaStream_t stream);

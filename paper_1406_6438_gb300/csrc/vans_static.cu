@@ -83,6 +83,10 @@ extern "C" int vans_step_static(const vans_params *p, const float *eps_dev, cons
         d.cb = (float)(1.75 / sqrt(150.0 * p->K));
     }
     d.cells = (long long)p->nx * p->ny * p->nz;
+    d.uw[0] = p->u_wall[0];
+    d.uw[1] = p->u_wall[1];
+    d.uw[2] = (p->q == 19) ? p->u_wall[2] : 0.f;
+    d.moving = (d.uw[0] != 0.f || d.uw[1] != 0.f || d.uw[2] != 0.f) ? 1 : 0;
     d.eps = eps_pad;
 
     cudaStream_t s = (cudaStream_t)cuda_stream;

@@ -71,6 +71,7 @@ __device__ __forceinline__ void step_row(const VDom &d, const float *__restrict_
             const bool wall = Y.wall[1 + L::ey(i)] || Z.wall[1 + L::ez(i)];
             et[i] = (i == 0 || wall) ? e0 : E[1 + L::ey(i)][1 + L::ez(i)][k + 1 + L::ex(i)];
         }
+        if (EDGE) apply_moving_wall<Q>(d, Y.wall[2], Z, e0, hh);
         float o[Q];
         collide<Q>(d, hh, e0, et, o);   // S2-S7
 #pragma unroll

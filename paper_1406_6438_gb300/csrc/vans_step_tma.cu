@@ -139,6 +139,7 @@ __global__ void __launch_bounds__(NT) k_step_tma(const VDom d, const float *__re
                             ? e0
                             : sb[(Q + eps_slot<Q>(L::ey(i), L::ez(i))) * SEG + 4 + xl + L::ex(i)];
             }
+            apply_moving_wall<Q>(d, Y.wall[2], Z, e0, h);
             collide<Q>(d, h, e0, et, o);
             if (x < d.nx) {
 #pragma unroll
@@ -294,6 +295,7 @@ __device__ __forceinline__ void ring_strip(const VDom &d, const float *__restric
                 const bool wall = Y.wall[1 + ey] || Z.wall[1 + ez];
                 et[i] = wall ? e0 : ey_slot[1 + ey][(Q == 9 ? 0 : 1 + ez) * SEG + 4 + xl + L::ex(i)];
             }
+            apply_moving_wall<Q>(d, Y.wall[2], Z, e0, h);
             collide<Q>(d, h, e0, et, o);
             if (x < d.nx) {
 #pragma unroll

@@ -31,6 +31,10 @@ ADJ_CASES = [
               K=4.0), 90, 30),
     (W.params(q=19, nx=12, ny=8, nz=6, wall_mask=6, tau=0.7, g=(1e-4, 0, 0), drag_mode=2,
               k_mode=0, d_p=5.0), 30, 10),
+    (W.params(q=9, nx=30, ny=20, wall_mask=2, tau=0.8, g=(5e-5, 0, 0), drag_mode=2, k_mode=2,
+              K=3.0, u_wall=(0.01, 0, 0)), 60, 20),
+    (W.params(q=19, nx=10, ny=7, nz=6, wall_mask=6, tau=0.75, g=(5e-5, 0, 0), drag_mode=2,
+              k_mode=0, d_p=5.0, u_wall=(0.01, 0.0, 0.004)), 24, 8),
 ]
 
 

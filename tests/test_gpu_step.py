@@ -212,3 +212,50 @@ def test_errors_reported():
     f[3, 0, 2, 2] = float("nan")          # a fault injected on the host side
     s.set_populations(f)
     assert not s.check()
+
+
+@pytest.mark.parametrize("Re,Da", [(1, 1e-3), (50, 1e-2)])
+def test_porous_couette_of_the_paper_80x80(Re, Da):
+    """The paper's validation case on the GPU: Couette flow through a porous
+    medium (eps = 0.1, 80 x 80, upper plate moving at u0, tau = 0.8, or 0.6574
+    at Re = 50), 3000 steps from rest, velocity within 1e-5 of the oracle."""
+    p, eps = W.couette_80(Re=Re, Da=Da)
+    rho_o, u_o, _ = oracle_run(p, eps, 3000)
+    rho, u, _ = gpu_run(p, eps, 3000)
+    assert rel_u(u, u_o) <= 1e-5, rel_u(u, u_o)
+    assert np.abs(rho - rho_o).max() <= 1e-5
+
+
+MOVING = [
+    (9, (1, 13, 37), 2, (0.01, 0.002, 0.0),
+     [Launch(4, 4, 1), Launch(1, 2, 1), Launch(2, 4, 3, 1), Launch(2, 4, 3, 2)]),
+    (9, (1, 1, 5), 2, (0.02, 0.0, 0.0), [Launch(2, 2, 1), Launch(2, 4, 2, 2)]),
+    (19, (7, 9, 21), 6, (0.01, 0.003, -0.002),
+     [Launch(1, 2, 1), Launch(2, 2, 2), Launch(1, 4, 3, 1), Launch(2, 4, 2, 2)]),
+    (19, (4, 5, 9), 2, (0.0, 0.0, 0.01), [Launch(2, 2, 1), Launch(1, 8, 2, 2)]),
+]
+
+
+@pytest.mark.parametrize("q,shape,wm,uw,launches", MOVING)
+def test_moving_wall_random_states(q, shape, wm, uw, launches):
+    """Populations through a moving upper wall (including the D3Q19 edge rows
+    where a z wall is crossed too), every kernel kind, 1 and 5 steps."""
+    p, eps, f0 = _case(q, shape, wm, seed=31 + sum(shape))
+    p["u_wall"] = tuple(W.f32(v) for v in uw)
+    for nsteps in (1, 5):
+        rho_o, u_o, f_o = oracle_run(p, eps, nsteps, f0)
+        for L in launches:
+            rho, u, f = gpu_run(p, eps, nsteps, f0, launch=L)
+            assert np.abs(f - f_o).max() <= 2e-7, (L, nsteps, np.abs(f - f_o).max())
+            assert rel_u(u, u_o) <= 1e-5, (L, nsteps)
+
+
+def test_rest_state_next_to_a_moving_wall():
+    """After vans_set_eps the populations are f = w eps everywhere, also in the
+    row under the moving plate (the initial state of the validation case)."""
+    torch = torch_cuda()
+    p, eps = W.couette_80(Re=50, Da=1e-2, nx=16)
+    s = solver(p, eps)
+    f = s.populations().cpu().numpy()
+    w = W.lattice_weights(9).reshape(9, 1, 1, 1)
+    assert np.abs(f - w * eps[None].astype(np.float64)).max() <= 1e-8

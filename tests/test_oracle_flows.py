@@ -174,3 +174,40 @@ def test_quiescent_porous_box_stays_near_rest():
     umax = np.abs(u).max()
     assert np.isfinite(umax) and umax < 1e-2
     assert abs(f.sum() - f0.sum()) <= 1e-12 * f0.sum()
+
+
+@pytest.mark.parametrize("tau", [0.6, 0.8, 1.3])
+def test_couette_linear_with_moving_wall(tau):
+    """eps = 1, no drag: plane Couette flow between a resting lower wall and an
+    upper wall moving at u0 is exactly linear at the nodes with half-way
+    bounce-back, u(y) = u0 y / H at y = j + 1/2, for any tau."""
+    H, u0 = 16, 1e-3
+    p = O.Params(q=9, nx=1, ny=H, wall_mask=2, tau=tau, u_wall=(u0, 0, 0))
+    eps = np.ones(p.shape)
+    f = O.run(p, eps, O.init(p, eps), 20000)
+    _, u = O.moments(p, eps, f)
+    y = np.arange(H) + 0.5
+    assert np.abs(u[0, 0, :, 0] - u0 * y / H).max() <= 1e-10 * u0
+    assert np.abs(u[1]).max() <= 1e-10 * u0
+
+
+def test_porous_couette_of_the_paper_against_bvp():
+    """The paper's validation case: Couette flow through a porous medium,
+    eps = 0.1, H = L = 80, Re = 1 (tau = 0.8), Da = 1e-3, upper plate at u0, drag
+    law with F_eps from eps.  Steady profile against a 4001-point Newton
+    solution of the paper's equation nu u'' - (eps nu/K) u - (eps^2 F_eps/sqrt K)
+    u^2 = 0, u(0) = 0, u(H) = u0 (the printed d/dx read as d/dy): within 0.2 %
+    of u0 (the paper shows "excellent agreement" in a figure only)."""
+    p, eps32 = W.couette_80(Re=1, Da=1e-3, nx=1)
+    po = O.Params(**p)
+    e = eps32.astype(np.float64)
+    f = O.run(po, e, O.init(po, e), 20000)
+    _, u = O.moments(po, e, f)
+    nu = CS2 * (p["tau"] - 0.5)
+    ee = float(eps32.flat[0])
+    Feps = 1.75 / np.sqrt(150 * ee ** 3)
+    u0 = p["u_wall"][0]
+    yb, ub = porous_bvp(nu, ee, p["K"], Feps, 0.0, 80, u_top=u0)
+    ref = np.interp(np.arange(80) + 0.5, yb, ub)
+    assert np.abs(u[0, 0, :, 0] - ref).max() <= 2e-3 * u0
+    assert 0.9 < u[0, 0, -1, 0] / u0 < 1.0
