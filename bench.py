@@ -236,11 +236,25 @@ def time_region(torch, stream, fn):
     return a.elapsed_time(b) / 1e3
 
 
-def bench_d3q19(torch, V, W):
-    p, eps, n = W.duct_3d()
+def fixed_launch(spec):
+    return None if not spec else tuple(int(v) for v in spec.split(","))
+
+
+def bench_d3q19(torch, V, W, args=None):
+    dims = dict(nx=256, ny=256, nz=256)
+    if args is not None and args.dims:
+        dims = dict(zip(("nx", "ny", "nz"), (int(v) for v in args.dims.split(","))))
+    p, eps, n = W.duct_3d(**dims)
+    if args is not None and args.only == "d3q19":
+        n = args.steps
     s = V.Solver(p)
     s.set_eps(torch.from_numpy(eps).cuda().view(-1))
-    L = s.autotune()
+    fl = fixed_launch(args.launch) if args is not None else None
+    if fl:
+        s.launch = V.Launch(*fl)
+        L = s.launch
+    else:
+        L = s.autotune()
     s.step(10)
     c0 = s.launch_count
     t = time_region(torch, s.stream, lambda: s.step(n))
@@ -253,13 +267,19 @@ def bench_d3q19(torch, V, W):
     return out
 
 
-def bench_batched(torch, V, W):
-    doms = W.batched_channels()
+def bench_batched(torch, V, W, args=None):
+    ndom = args.domains if args is not None and args.domains else 256
+    doms = W.batched_channels(n=ndom)
     b = V.Batch([p for p, _ in doms])
     for d, (_, eps) in enumerate(doms):
         b.set_eps(d, torch.from_numpy(eps).cuda().view(-1))
-    L = b.autotune()
-    n = 2000
+    fl = fixed_launch(args.launch) if args is not None else None
+    if fl:
+        b.launch = V.Launch(*fl)
+        L = b.launch
+    else:
+        L = b.autotune()
+    n = args.steps if args is not None and args.only == "batched" else 2000
     b.step(20)
     c0 = b.launch_count
     t = time_region(torch, b.stream, lambda: b.step(n))
@@ -273,9 +293,12 @@ def bench_batched(torch, V, W):
     return out
 
 
-def bench_adjoint(torch, V, W):
+def bench_adjoint(torch, V, W, args=None):
     from paper_1406_6438_gb300.adjoint import outlet_flux
-    p, eps, n, every = W.adjoint_channel()
+    if args is not None and args.only == "adjoint":
+        p, eps, n, every = W.adjoint_channel(nsteps=args.steps, every=min(100, args.steps))
+    else:
+        p, eps, n, every = W.adjoint_channel()
     cells = p["nx"] * p["ny"]
     out = {"workload": "D2Q9 512x512 channel, eps noise [0.4,1.0], tau 0.8, outlet flux gradient",
            "steps": n, "checkpoint_every": every, "unit": "MLUPS (backward pass, wall clock)"}
@@ -318,10 +341,21 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--launch", default=None,
                     help="fixed launch shape cpt,warps,rows[,kind] instead of the autotuner")
+    ap.add_argument("--only", default=None, choices=["d3q19", "batched", "adjoint"],
+                    help="run one side benchmark alone (profiling captures) and print its JSON")
+    ap.add_argument("--dims", default=None, help="nx,ny,nz of the D3Q19 duct for --only d3q19")
+    ap.add_argument("--domains", type=int, default=0, help="domains for --only batched")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return reference_arm(args)
+    if args.only:
+        import torch
+        import paper_1406_6438_gb300 as V
+        from paper_1406_6438_gb300 import workloads as W
+        fn = {"d3q19": bench_d3q19, "batched": bench_batched, "adjoint": bench_adjoint}[args.only]
+        print(json.dumps({args.only: fn(torch, V, W, args)}), flush=True)
+        return 0
 
     import torch
     import paper_1406_6438_gb300 as V

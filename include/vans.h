@@ -128,12 +128,33 @@ void vans_destroy(vans_t h);
  * previous state.  (Synchronises the stream once to check the range.) */
 int vans_set_eps(vans_t h, const float *eps_dev);
 
+/* Replace the porosity field by eps_dev (dense, 0 < eps <= 1 else
+ * VANS_ERR_ARG and nothing changes) while keeping the physical populations
+ * f_i(x, t) of the current state: a porosity that varies in time, the
+ * direction the paper names for two-fluid models (its concluding section).
+ * The stored deviations are re-expressed for the new eps in place.
+ * Synchronises once to check the range.  VANS_ERR_STATE before vans_set_eps. */
+int vans_update_eps(vans_t h, const float *eps_dev);
+
 /* ----------------------------------------------------------- time step -- */
 
 /* Advance the current state by nsteps >= 0 steps of the final LBE with P_i and
  * F_i.  Long runs replay a captured CUDA graph.  Errors: VANS_ERR_STATE before
  * vans_set_eps, VANS_ERR_ARG for nsteps < 0, VANS_ERR_CUDA. */
 int vans_step(vans_t h, int nsteps);
+
+/* nsteps steps that watch themselves (no extra pass over the populations):
+ * the last step of every block of `every` steps (every >= 1; also the last of
+ * the call) writes rho (dense N floats) and u (dense D*N floats) of the state
+ * it reads -- the moments of Eqs. 0moment and 1moment, as vans_moments gives --
+ * and reduces, over all cells, into stats_dev (device float[4], cleared at the
+ * call): [0] max |u - u_prev| with u_prev what u_dev held before that step
+ * (convergence; the first comparison is against u_dev's contents on entry),
+ * [1] max |u|, [2] 1.0 if a non-finite state or |u| >= 0.5 was met, [3] the
+ * number of monitoring steps.  Stats [0] and [1] are the maxima over all
+ * monitoring steps of the call. */
+int vans_step_monitored(vans_t h, int nsteps, int every, float *rho_dev, float *u_dev,
+                        float *stats_dev);
 
 /* One step from the caller's state buffer `in` to the caller's state buffer
  * `out` (both vans_state_floats() floats; they must not overlap).  Uses the

@@ -124,8 +124,10 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
                                            ctypes.POINTER(_H)]),
             "vans_destroy": (None, [_H]),
             "vans_set_eps": (ctypes.c_int, [_H, _F]),
+            "vans_update_eps": (ctypes.c_int, [_H, _F]),
             "vans_step": (ctypes.c_int, [_H, ctypes.c_int]),
             "vans_step_raw": (ctypes.c_int, [_H, _F, _F]),
+            "vans_step_monitored": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int, _F, _F, _F]),
             "vans_moments": (ctypes.c_int, [_H, _F, _F]),
             "vans_get_populations": (ctypes.c_int, [_H, _F]),
             "vans_set_populations": (ctypes.c_int, [_H, _F]),
@@ -236,8 +238,29 @@ class Solver:
     def set_eps(self, eps):
         _check(self.lib.vans_set_eps(self._h, _f32(eps, self.params.cells, "eps")), "vans_set_eps")
 
+    def update_eps(self, eps):
+        """New porosity field, same physical populations (eps varying in time)."""
+        _check(self.lib.vans_update_eps(self._h, _f32(eps, self.params.cells, "eps")),
+               "vans_update_eps")
+
     def step(self, nsteps: int = 1):
         _check(self.lib.vans_step(self._h, int(nsteps)), "vans_step")
+
+    def step_monitored(self, nsteps: int, every: int, rho=None, u=None, stats=None):
+        """nsteps steps; every `every` steps the step kernel also writes rho and u
+        and reduces (max|du|, max|u|, diverged, count) into stats."""
+        torch = _torch()
+        p = self.params
+        if rho is None:
+            rho = torch.empty(p.shape, dtype=torch.float32, device=self.device)
+        if u is None:
+            u = torch.zeros((p.dim,) + p.shape, dtype=torch.float32, device=self.device)
+        if stats is None:
+            stats = torch.empty(4, dtype=torch.float32, device=self.device)
+        _check(self.lib.vans_step_monitored(self._h, int(nsteps), int(every),
+                                            _f32(rho, p.cells, "rho"), _f32(u, p.dim * p.cells, "u"),
+                                            _f32(stats, 4, "stats")), "vans_step_monitored")
+        return rho, u, stats
 
     def step_raw(self, state_in, state_out):
         _check(self.lib.vans_step_raw(self._h, _f32(state_in, self.state_floats, "state_in"),

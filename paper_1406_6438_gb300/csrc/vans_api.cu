@@ -443,10 +443,55 @@ int vans_set_eps(vans_t h, const float *eps_dev) {
     return VANS_OK;
 }
 
+int vans_update_eps(vans_t h, const float *eps_dev) {
+    if (!h || h->batched || !eps_dev) return VANS_ERR_ARG;
+    if (!h->eps_set) return VANS_ERR_STATE;
+    if (cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream) != cudaSuccess) return VANS_ERR_CUDA;
+    ++h->launches;
+    if (vans::launch_pad_eps(h->dom, eps_dev, nullptr, h->flag, h->stream) != cudaSuccess)
+        return VANS_ERR_CUDA;
+    int bad = 0;
+    int rc = read_flag(h, &bad);
+    if (rc) return rc;
+    if (bad) return VANS_ERR_ARG;
+    h->launches += 2;
+    if (vans::launch_rebase_eps(h->q, h->dom, eps_dev, h->st[h->cur], h->stream) != cudaSuccess)
+        return VANS_ERR_CUDA;
+    if (vans::launch_pad_eps(h->dom, eps_dev, h->eps_pad, h->flag, h->stream) != cudaSuccess)
+        return VANS_ERR_CUDA;
+    return VANS_OK;
+}
+
 int vans_step(vans_t h, int nsteps) {
     if (!h || h->batched || nsteps < 0) return VANS_ERR_ARG;
     if (!h->eps_set) return VANS_ERR_STATE;
     return run_steps(h, nsteps);
+}
+
+int vans_step_monitored(vans_t h, int nsteps, int every, float *rho_dev, float *u_dev,
+                        float *stats_dev) {
+    if (!h || h->batched || nsteps < 0 || every < 1 || !rho_dev || !u_dev || !stats_dev)
+        return VANS_ERR_ARG;
+    if (!h->eps_set) return VANS_ERR_STATE;
+    if (cudaMemsetAsync(stats_dev, 0, 4 * sizeof(float), h->stream) != cudaSuccess)
+        return VANS_ERR_CUDA;
+    int done = 0;
+    while (done < nsteps) {
+        // every-1 plain steps (graph-replayed when long), then one monitoring step
+        const int plain = std::min(every - 1, nsteps - done - 1);
+        if (plain > 0) {
+            const int rc = run_steps(h, plain);
+            if (rc) return rc;
+            done += plain;
+        }
+        ++h->launches;
+        if (vans::launch_step_monitor(h->q, h->dom, h->st[h->cur], h->st[h->cur ^ 1], rho_dev, u_dev,
+                                      stats_dev, h->stream) != cudaSuccess)
+            return VANS_ERR_CUDA;
+        h->cur ^= 1;
+        ++done;
+    }
+    return VANS_OK;
 }
 
 int vans_step_raw(vans_t h, const float *in, float *out) {

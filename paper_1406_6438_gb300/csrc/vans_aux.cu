@@ -146,6 +146,34 @@ __global__ void k_init_moving(const VDom d, float *__restrict__ st) {
     }
 }
 
+// A new porosity field under an unchanged physical state f: every live entry
+// stores f - w eps~ (minus the moving-wall gain where one applies), so it is
+// re-expressed from the old eps (the padded rows still in d.eps) to the new
+// one (dense eps_new).  Each entry belongs to exactly one cell (pull_index is
+// a bijection), so the update runs in place.
+template <int Q>
+__global__ void k_rebase_eps(const VDom d, const float *__restrict__ eps_new, float *__restrict__ st) {
+    using L = Lat<Q>;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < d.cells;
+         n += (long long)gridDim.x * blockDim.x) {
+        int x, y, z;
+        cell_xyz(d, n, x, y, z);
+        Nb3 Y, Z;
+        nb_yz<Q>(d, y, z, Y, Z);
+        const float e_old = d.eps[row_offset(d, y, z) + x];
+        const float e_new = eps_new[n];
+        const bool top = d.moving && Y.wall[2];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const long long k = pull_index<Q>(d, i, x, y, z, Y, Z);
+            float v = st[k] + L::w(i) * (e_old - e_new);
+            if (top && L::ey(i) < 0 && !Z.wall[1 - L::ez(i)])
+                v += wall_gain<Q>(d, i, e_old) - wall_gain<Q>(d, i, e_new);
+            st[k] = v;
+        }
+    }
+}
+
 // eps into padded rows with periodic halo columns; padding gets 1.0.  Flags any
 // value outside (0, 1] (NaN included).
 __global__ void k_pad_eps(const VDom d, const float *__restrict__ eps, float *__restrict__ pad,
@@ -479,6 +507,14 @@ cudaError_t launch_pad_eps(const VDom &d, const float *eps_dense, float *eps_pad
                            cudaStream_t s) {
     const int g = grid_for((long long)d.rows * d.pitch, 256);
     k_pad_eps<<<g, 256, 0, s>>>(d, eps_dense, eps_pad, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rebase_eps(int q, const VDom &d, const float *eps_new, float *state,
+                              cudaStream_t s) {
+    const int g = grid_for(d.cells, 256);
+    VANS_DISPATCH_Q(q, (k_rebase_eps<9><<<g, 256, 0, s>>>(d, eps_new, state)),
+                    (k_rebase_eps<19><<<g, 256, 0, s>>>(d, eps_new, state)));
     return cudaGetLastError();
 }
 

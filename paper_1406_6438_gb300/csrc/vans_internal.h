@@ -54,6 +54,8 @@ struct Launch {
 
 cudaError_t launch_step(int q, const VDom &d, const float *fin, float *fout, Launch L,
                         cudaStream_t stream);
+cudaError_t launch_step_monitor(int q, const VDom &d, const float *fin, float *fout, float *rho,
+                                float *u, float *stats, cudaStream_t stream);
 cudaError_t launch_step_tma(int q, const VDom &d, const float *fin, float *fout, Launch L,
                             cudaStream_t stream);
 cudaError_t launch_ring_batched(const VDom *doms, const Tile *strips, int nstrips, int parity,
@@ -67,6 +69,8 @@ cudaError_t launch_export(int q, const VDom &d, const float *state, float *f, cu
 cudaError_t launch_import(int q, const VDom &d, const float *f, float *state, cudaStream_t stream);
 cudaError_t launch_pad_eps(const VDom &d, const float *eps_dense, float *eps_pad, int *flag,
                            cudaStream_t stream);
+cudaError_t launch_rebase_eps(int q, const VDom &d, const float *eps_new, float *state,
+                              cudaStream_t stream);
 cudaError_t launch_init_moving(int q, const VDom &d, float *state, cudaStream_t stream);
 cudaError_t launch_check(int q, const VDom &d, const float *state, int *flag, cudaStream_t stream);
 cudaError_t launch_flux(int q, const VDom &d, const float *state, int x_out, float *J,

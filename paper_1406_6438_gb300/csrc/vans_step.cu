@@ -15,9 +15,24 @@
 
 namespace vans {
 
-template <int Q, int CPT, bool EDGE>
+// Outputs of a monitoring step (vans_step_monitored): rho and u of the state
+// the step reads, and reductions into stats = {max |u - u_prev|, max |u|,
+// diverged (1.0f), emissions}.
+struct Monitor {
+    float *rho;
+    float *u;
+    float *stats;
+};
+
+__device__ __forceinline__ void atomic_max_nonneg(float *a, float v) {
+    // non-negative floats order like their bit patterns
+    atomicMax(reinterpret_cast<int *>(a), __float_as_int(v));
+}
+
+template <int Q, int CPT, bool EDGE, bool EMIT = false>
 __device__ __forceinline__ void step_row(const VDom &d, const float *__restrict__ fin,
-                                         float *__restrict__ fout, int y, int z, int x0, int lane) {
+                                         float *__restrict__ fout, int y, int z, int x0, int lane,
+                                         const Monitor *mon = nullptr) {
     using L = Lat<Q>;
     const Nb3 Y = nb3<EDGE>(y, d.ny, d.wall_y);
     Nb3 Z;
@@ -61,6 +76,8 @@ __device__ __forceinline__ void step_row(const VDom &d, const float *__restrict_
     }
 
     float out[Q][CPT];
+    float dmax = 0.f, umax = 0.f;
+    bool bad = false;
 #pragma unroll
     for (int k = 0; k < CPT; ++k) {
         float hh[Q], et[Q];
@@ -72,10 +89,43 @@ __device__ __forceinline__ void step_row(const VDom &d, const float *__restrict_
             et[i] = (i == 0 || wall) ? e0 : E[1 + L::ey(i)][1 + L::ez(i)][k + 1 + L::ex(i)];
         }
         if (EDGE) apply_moving_wall<Q>(d, Y.wall[2], Z, e0, hh);
+        if (EMIT) {
+            // S8 fused into the step: the moments of the state this step reads
+            Macro<Q> M;
+            macro<Q>(d, hh, e0, et, M);
+            if (x0 + k < d.nx) {
+                const long long n = ((long long)z * d.ny + y) * d.nx + x0 + k;
+                mon->rho[n] = M.rho;
+                float du2 = 0.f;
+#pragma unroll
+                for (int c = 0; c < L::D; ++c) {
+                    const float prev = mon->u[c * d.cells + n];
+                    du2 += (M.u[c] - prev) * (M.u[c] - prev);
+                    mon->u[c * d.cells + n] = M.u[c];
+                }
+                dmax = fmaxf(dmax, sqrtf(du2));
+                umax = fmaxf(umax, M.un);
+                bad = bad || !isfinite(M.R) || !isfinite(M.un) || !(M.un < 0.5f);
+            }
+        }
         float o[Q];
         collide<Q>(d, hh, e0, et, o);   // S2-S7
 #pragma unroll
         for (int i = 0; i < Q; ++i) out[i][k] = o[i];
+    }
+    if (EMIT) {
+        // warp maxima, one atomic per warp
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            dmax = fmaxf(dmax, __shfl_xor_sync(VANS_FULL, dmax, off));
+            umax = fmaxf(umax, __shfl_xor_sync(VANS_FULL, umax, off));
+        }
+        bad = __any_sync(VANS_FULL, bad);
+        if (lane == 0) {
+            atomic_max_nonneg(&mon->stats[0], bad ? 0.f : dmax);
+            atomic_max_nonneg(&mon->stats[1], bad ? 0.f : umax);
+            if (bad) atomic_max_nonneg(&mon->stats[2], 1.f);
+        }
     }
 
     const long long ro = row_offset(d, y, z);
@@ -98,9 +148,9 @@ __device__ __forceinline__ void step_row(const VDom &d, const float *__restrict_
     }
 }
 
-template <int Q, int CPT>
+template <int Q, int CPT, bool EMIT = false>
 __global__ void __launch_bounds__(256) k_step(const VDom d, const float *__restrict__ fin,
-                                              float *__restrict__ fout, int nxb) {
+                                              float *__restrict__ fout, int nxb, Monitor mon = {}) {
     const int lane = threadIdx.x & 31;
     const int wx = threadIdx.x >> 5;
     const int bx = blockIdx.x % nxb;
@@ -113,9 +163,10 @@ __global__ void __launch_bounds__(256) k_step(const VDom d, const float *__restr
     const int y = r % d.ny, z = r / d.ny;
     const bool edge = (y == 0) || (y == d.ny - 1) || (Q == 19 && (z == 0 || z == d.nz - 1));
     if (edge)
-        step_row<Q, CPT, true>(d, fin, fout, y, z, x0, lane);
+        step_row<Q, CPT, true, EMIT>(d, fin, fout, y, z, x0, lane, &mon);
     else
-        step_row<Q, CPT, false>(d, fin, fout, y, z, x0, lane);
+        step_row<Q, CPT, false, EMIT>(d, fin, fout, y, z, x0, lane, &mon);
+    if (EMIT && blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) atomicAdd(&mon.stats[3], 1.f);
 }
 
 // Batched D2Q9: one persistent grid walks a flattened list of equal-shaped
@@ -175,6 +226,24 @@ cudaError_t launch_step(int q, const VDom &d, const float *fin, float *fout, Lau
         }
     }
     return cudaErrorInvalidValue;
+}
+
+// A monitoring step: the register-load kernel (4 cells per lane, 4 warps) with
+// the moment outputs and reductions switched on.
+cudaError_t launch_step_monitor(int q, const VDom &d, const float *fin, float *fout, float *rho,
+                                float *u, float *stats, cudaStream_t stream) {
+    constexpr int CPT = 4, WARPS = 4;
+    const int nxb = (d.nx + 32 * CPT * WARPS - 1) / (32 * CPT * WARPS);
+    const long long nblocks = (long long)nxb * d.rows;
+    if (nblocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    const Monitor mon{rho, u, stats};
+    if (q == 9)
+        k_step<9, CPT, true><<<(unsigned)nblocks, 32 * WARPS, 0, stream>>>(d, fin, fout, nxb, mon);
+    else if (q == 19)
+        k_step<19, CPT, true><<<(unsigned)nblocks, 32 * WARPS, 0, stream>>>(d, fin, fout, nxb, mon);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
 }
 
 int batched_blocks_per_sm(Launch L) {

@@ -259,3 +259,71 @@ def test_rest_state_next_to_a_moving_wall():
     f = s.populations().cpu().numpy()
     w = W.lattice_weights(9).reshape(9, 1, 1, 1)
     assert np.abs(f - w * eps[None].astype(np.float64)).max() <= 1e-8
+
+
+@pytest.mark.parametrize("q,shape,wm,uw", [(9, (1, 30, 41), 2, (0.0, 0.0, 0.0)),
+                                         (9, (1, 24, 33), 2, (0.01, 0.0, 0.0)),
+                                         (19, (8, 10, 17), 6, (0.0, 0.0, 0.0))])
+def test_porosity_varying_in_time(q, shape, wm, uw):
+    """eps(x, t): the field changes every few steps (a translating smoothed
+    field) while the populations carry on; the oracle runs the same schedule
+    on its own state.  Velocity within 1e-5 after 60 steps."""
+    torch = torch_cuda()
+    import oracle as O
+    nz, ny, nx = shape
+    p = W.params(q=q, nx=nx, ny=ny, nz=nz, wall_mask=wm, tau=0.7, g=(4e-5, 0, 0),
+                 drag_mode=2, k_mode=0, d_p=6.0, u_wall=uw)
+    base = W.smoothed_noise(shape, 3.0, 0.4, 1.0, seed=51)
+    fields = [np.ascontiguousarray(np.roll(base, k, axis=2)) for k in range(6)]
+    s = solver(p, fields[0])
+    po = O.Params(**p)
+    f = O.init(po, fields[0].astype(np.float64))
+    for k, e in enumerate(fields):
+        if k:
+            s.update_eps(torch.from_numpy(e).cuda().view(-1))
+        s.step(10)
+        f = O.run(po, e.astype(np.float64), f, 10)
+    rho, u = s.moments()
+    torch.cuda.synchronize()
+    rho_o, u_o = O.moments(po, fields[-1].astype(np.float64), f)
+    assert rel_u(u.cpu().numpy().astype(np.float64), u_o) <= 1e-5
+    assert np.abs(rho.cpu().numpy() - rho_o).max() <= 1e-5
+    # the populations survive the update itself
+    fa = s.populations()
+    s.update_eps(torch.from_numpy(fields[0]).cuda().view(-1))
+    fb = s.populations()
+    torch.cuda.synchronize()
+    assert (fa - fb).abs().max().item() <= 1e-7
+
+
+def test_monitored_steps_emit_the_moments_and_reductions():
+    """vans_step_monitored: the moments written by the step kernel equal those of
+    vans_moments on the same state, the run itself matches plain steps, and the
+    in-kernel reductions report max |u|, the change since the last emission,
+    the number of emissions and a divergence."""
+    torch = torch_cuda()
+    p, eps, _ = W.periodic_2d_shape(150, 70, nsteps=0)
+    a = solver(p, eps)
+    b = solver(p, eps)
+    a.step(40)
+    rho_ref, u_ref = a.moments()                 # state after 40 steps
+    rho, u, st = b.step_monitored(41, 41)        # one emission, reading the state after 40
+    torch.cuda.synchronize()
+    assert (rho - rho_ref).abs().max().item() <= 1e-6
+    assert (u - u_ref).abs().max().item() <= 1e-6 * u_ref.abs().max().item() + 1e-12
+    s = st.cpu().numpy()
+    assert s[3] == 1.0 and s[2] == 0.0
+    assert abs(s[1] - float(torch.linalg.vector_norm(u_ref, dim=0).max())) <= 1e-6 * s[1]
+    assert abs(s[0] - s[1]) <= 1e-6 * s[1]       # previous u was zero
+    a.step(1)
+    assert (a.populations() - b.populations()).abs().max().item() <= 1e-7
+    # several emissions; converging flow reports a small change between them
+    rho, u, st = b.step_monitored(300, 100, rho, u)
+    s = st.cpu().numpy()
+    assert s[3] == 3.0 and 0.0 < s[0] < s[1]
+    # a non-finite state is flagged
+    f = b.populations()
+    f[2, 0, 5, 5] = float("nan")
+    b.set_populations(f)
+    _, _, st = b.step_monitored(1, 1, rho, u)
+    assert st[2].item() == 1.0
