@@ -220,6 +220,11 @@ int vans_step_adjoint(vans_t h, const float *state_t, const float *lam_in, float
 int vans_adjoint_segment(vans_t h, const float *ckpt, float *seg, int len, float *lam, float *tmp,
                          float *grad_acc);
 
+/* Launch shape of the reverse step: cpt cells per lane (1, or 2 for D2Q9),
+ * `warps` x `rows` threads per block (at most 8 warps), kind 0.  VANS_ERR_ARG
+ * otherwise. */
+int vans_set_adjoint_launch(vans_t h, const vans_launch *cfg);
+
 /* Arithmetic of the per-cell reverse step: 32 (FP32, the default) or 64 (FP64;
  * loads, stores and the compensated accumulation stay FP32).  The eps gradient
  * is a small residual of large grad-eps sensitivities, so FP32 per-cell

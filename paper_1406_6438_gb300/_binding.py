@@ -142,6 +142,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
             "vans_grad_finalize": (ctypes.c_int, [_H, _F, _F, _F]),
             "vans_adjoint_segment": (ctypes.c_int, [_H, _F, _F, ctypes.c_int, _F, _F, _F]),
             "vans_set_adjoint_precision": (ctypes.c_int, [_H, ctypes.c_int]),
+            "vans_set_adjoint_launch": (ctypes.c_int, [_H, _LP]),
             "vans_batch_workspace_bytes": (ctypes.c_size_t, [_P, ctypes.c_int]),
             "vans_batch_create": (ctypes.c_int, [_P, ctypes.c_int, _F, ctypes.c_size_t,
                                                  ctypes.c_void_p, ctypes.POINTER(_H)]),
@@ -361,6 +362,10 @@ class Solver:
                                           _f32(lam_out, self.state_floats, "lam_out"),
                                           _f32(grad, self.grad_floats(), "grad_acc")),
                "vans_step_adjoint")
+
+    def set_adjoint_launch(self, L: Launch):
+        c = _CLaunch(int(L.cpt), int(L.warps), int(L.rows), int(L.kind))
+        _check(self.lib.vans_set_adjoint_launch(self._h, ctypes.byref(c)), "vans_set_adjoint_launch")
 
     def set_adjoint_precision(self, bits: int):
         _check(self.lib.vans_set_adjoint_precision(self._h, int(bits)), "vans_set_adjoint_precision")

@@ -132,6 +132,7 @@ struct vans_s {
     cudaGraphExec_t gexec = nullptr;
     int *flag = nullptr;                        // device status words (workspace)
     int adj_fp64 = 0;                           // reverse-step arithmetic in FP64
+    Launch adjL{1, 4, 2, 0};                    // reverse-step launch shape
     // single domain
     vans_params p{};
     VDom dom{};
@@ -397,6 +398,7 @@ int vans_create(const vans_params *p, void *workspace, size_t workspace_bytes, v
     h->dom.eps = h->eps_pad;
     h->dom.status = h->flag + 1;
     h->L = (p->q == 9) ? Launch{4, 4, 1, 0} : Launch{2, 4, 1, 0};
+    h->adjL = Launch{1, 4, 2, 0};   // one cell per lane: fastest on GB300 at 512^2 (17.8 vs 22.5 us)
     int rc = make_streams(h, cuda_stream);
     if (rc) {
         vans_destroy(h);
@@ -618,7 +620,7 @@ int vans_step_adjoint(vans_t h, const float *state_t, const float *lam_in, float
     if (!h->eps_set) return VANS_ERR_STATE;
     ++h->launches;
     return cuda_status(vans::launch_step_adjoint(h->q, h->dom, state_t, lam_in, lam_out, grad_acc,
-                                                 h->adj_fp64, h->stream));
+                                                 h->adj_fp64, h->adjL, h->stream));
 }
 
 int vans_adjoint_segment(vans_t h, const float *ckpt, float *seg, int len, float *lam, float *tmp,
@@ -649,7 +651,7 @@ int vans_adjoint_segment(vans_t h, const float *ckpt, float *seg, int len, float
         float *a = lam, *b = tmp;
         for (int k = len - 1; k >= 0 && le == cudaSuccess; --k) {
             le = vans::launch_step_adjoint(h->q, h->dom, seg + k * sf, a, b, grad_acc, h->adj_fp64,
-                                           h->cap);
+                                           h->adjL, h->cap);
             float *t = a;
             a = b;
             b = t;
@@ -670,6 +672,15 @@ int vans_adjoint_segment(vans_t h, const float *ckpt, float *seg, int len, float
     }
     if (cudaGraphLaunch(g->exec, h->stream) != cudaSuccess) return VANS_ERR_CUDA;
     h->launches += 2LL * len;
+    return VANS_OK;
+}
+
+int vans_set_adjoint_launch(vans_t h, const vans_launch *cfg) {
+    if (!h || h->batched || !cfg) return VANS_ERR_ARG;
+    if (cfg->kind != 0 || cfg->warps < 1 || cfg->rows < 1 || cfg->warps * cfg->rows > 8) return VANS_ERR_ARG;
+    if (!(cfg->cpt == 1 || (cfg->cpt == 2 && h->q == 9))) return VANS_ERR_ARG;
+    h->adjL = Launch{cfg->cpt, cfg->warps, cfg->rows, 0};
+    drop_graph(h);
     return VANS_OK;
 }
 

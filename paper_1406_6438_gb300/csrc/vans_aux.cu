@@ -552,22 +552,32 @@ cudaError_t launch_flux_seed(int q, const VDom &d, const float *state, int x_out
     return cudaGetLastError();
 }
 
-cudaError_t launch_step_adjoint(int q, const VDom &d, const float *state, const float *lam_in,
-                                float *lam_out, float *grad, int fp64, cudaStream_t s) {
-    // two cells per lane for D2Q9, one for D3Q19 (register pressure); 4 warps x 2 rows
-    const int warps = 4, rows = 2;
-    const int cpt = (q == 9) ? 2 : 1;
-    const int nxb = (d.nx + 32 * cpt * warps - 1) / (32 * cpt * warps);
-    const int nrb = (d.rows + rows - 1) / rows;
-    dim3 block(32 * warps, rows);
-    const unsigned nb = (unsigned)((long long)nxb * nrb);
-    if (fp64)
-        VANS_DISPATCH_Q(q, (k_step_adjoint<9, 2, double><<<nb, block, 0, s>>>(d, state, lam_in, lam_out, grad, nxb)),
-                        (k_step_adjoint<19, 1, double><<<nb, block, 0, s>>>(d, state, lam_in, lam_out, grad, nxb)));
-    else
-        VANS_DISPATCH_Q(q, (k_step_adjoint<9, 2, float><<<nb, block, 0, s>>>(d, state, lam_in, lam_out, grad, nxb)),
-                        (k_step_adjoint<19, 1, float><<<nb, block, 0, s>>>(d, state, lam_in, lam_out, grad, nxb)));
+template <int Q, int CPT, typename T>
+static cudaError_t launch_adj_t(const VDom &d, const float *state, const float *lam_in,
+                                float *lam_out, float *grad, Launch L, cudaStream_t s) {
+    const int nxb = (d.nx + 32 * CPT * L.warps - 1) / (32 * CPT * L.warps);
+    const int nrb = (d.rows + L.rows - 1) / L.rows;
+    const long long nb = (long long)nxb * nrb;
+    if (nb > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    dim3 block(32 * L.warps, L.rows);
+    k_step_adjoint<Q, CPT, T><<<(unsigned)nb, block, 0, s>>>(d, state, lam_in, lam_out, grad, nxb);
     return cudaGetLastError();
+}
+
+// L.cpt: cells per lane (1 or 2; D3Q19 takes 1), L.warps x L.rows threads per block
+cudaError_t launch_step_adjoint(int q, const VDom &d, const float *state, const float *lam_in,
+                                float *lam_out, float *grad, int fp64, Launch L, cudaStream_t s) {
+    if (L.warps < 1 || L.rows < 1 || L.warps * L.rows > 8) return cudaErrorInvalidValue;
+    if (q == 9 && L.cpt == 2)
+        return fp64 ? launch_adj_t<9, 2, double>(d, state, lam_in, lam_out, grad, L, s)
+                    : launch_adj_t<9, 2, float>(d, state, lam_in, lam_out, grad, L, s);
+    if (q == 9 && L.cpt == 1)
+        return fp64 ? launch_adj_t<9, 1, double>(d, state, lam_in, lam_out, grad, L, s)
+                    : launch_adj_t<9, 1, float>(d, state, lam_in, lam_out, grad, L, s);
+    if (q == 19 && L.cpt == 1)
+        return fp64 ? launch_adj_t<19, 1, double>(d, state, lam_in, lam_out, grad, L, s)
+                    : launch_adj_t<19, 1, float>(d, state, lam_in, lam_out, grad, L, s);
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_grad_finalize(int q, const VDom &d, const float *lam0, const float *grad,

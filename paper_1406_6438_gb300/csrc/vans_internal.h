@@ -78,7 +78,8 @@ cudaError_t launch_flux(int q, const VDom &d, const float *state, int x_out, flo
 cudaError_t launch_flux_seed(int q, const VDom &d, const float *state, int x_out, float *lam,
                              float *grad, int fp64, cudaStream_t stream);
 cudaError_t launch_step_adjoint(int q, const VDom &d, const float *state, const float *lam_in,
-                                float *lam_out, float *grad, int fp64, cudaStream_t stream);
+                                float *lam_out, float *grad, int fp64, Launch L,
+                                cudaStream_t stream);
 cudaError_t launch_grad_finalize(int q, const VDom &d, const float *lam0, const float *grad,
                                  float *dJ, cudaStream_t stream);
 
