@@ -88,6 +88,8 @@ typedef struct {
  * kind 2: the kind-1 pipeline where each CTA walks a strip of consecutive rows
  *         (one column block, one z plane) and keeps the porosity rows in a
  *         shared-memory ring, so each eps row is read from HBM once per strip.
+ * kind 3: D2Q9 only: kind 2 with each thread on 4 consecutive cells (cpt 4,
+ *         warps 2 or 4): 16-byte shared loads and global stores.
  *         The batched path takes kinds 0 and 2 (kind 2: one CTA per strip of
  *         up to 32 rows of one domain). */
 typedef struct {

@@ -110,10 +110,11 @@ bool launch_ok(const vans_launch *c, int q, bool batched) {
         if (c->warps < 1 || c->warps > 8 || c->rows < 1 || c->rows > 8) return false;
         return c->warps * c->rows <= 8;
     }
-    if ((c->kind != 1 && c->kind != 2) || (batched && c->kind != 2)) return false;
+    if (c->kind < 1 || c->kind > 3 || (batched && c->kind != 2)) return false;
     if (c->rows < 2 || c->rows > 6) return false;
     // the instantiated pipeline shapes
     const int nt = 32 * c->warps;
+    if (c->kind == 3) return q == 9 && c->cpt == 4 && (nt == 64 || nt == 128);
     if (q == 9)
         return (nt == 128 && (c->cpt == 2 || c->cpt == 4)) || (nt == 256 && c->cpt <= 2);
     return (nt == 128 && c->cpt <= 2) || (nt == 256 && c->cpt == 1);
@@ -348,8 +349,9 @@ std::vector<Launch> candidates(int q, bool batched) {
         const Launch t[] = {{2, 4, 3, 1}, {2, 4, 4, 1}, {4, 4, 2, 1}, {4, 4, 3, 1},
                             {1, 8, 3, 1}, {1, 8, 4, 1}, {2, 8, 2, 1}, {2, 8, 3, 1},
                             {2, 4, 3, 2}, {2, 4, 4, 2}, {4, 4, 3, 2}, {1, 8, 3, 2},
-                            {1, 8, 4, 2}, {2, 8, 3, 2}};
-        c.insert(c.end(), t, t + 14);
+                            {1, 8, 4, 2}, {2, 8, 3, 2}, {4, 4, 2, 3}, {4, 4, 3, 3},
+                            {4, 2, 3, 3}, {4, 2, 4, 3}};
+        c.insert(c.end(), t, t + 18);
     } else {
         const Launch t[] = {{1, 4, 3, 1}, {1, 4, 4, 1}, {2, 4, 2, 1}, {2, 4, 3, 1},
                             {1, 8, 2, 1}, {1, 8, 3, 1}, {1, 4, 3, 2}, {2, 4, 2, 2},

@@ -229,8 +229,94 @@ __device__ __forceinline__ void issue_tile_ring(const VDom &d, const float *__re
     }
 }
 
+// Compute of one staged D2Q9 tile with each thread on 4 consecutive cells
+// (columns x0l..x0l+3 of the tile): each population row comes in one or two
+// aligned 16-byte shared loads and each output plane leaves in one 16-byte
+// global store, a quarter of the load/store instructions of the strided
+// mapping.  Segment position p holds column xs - 4 + p.
+template <int NT>
+__device__ __forceinline__ void ring_tile_vec9(const VDom &d, const float *__restrict__ sb,
+                                               const float *const ey_slot[3], const Nb3 &Y,
+                                               const Nb3 &Z, float *__restrict__ fout, long long ro,
+                                               int xs, int tid) {
+    using L = Lat<9>;
+    constexpr int SEG = NT * 4 + 8;
+    const int x0l = 4 * tid;
+    auto v4 = [&](const float *row, int p, float out[4]) {
+        const float4 t = *reinterpret_cast<const float4 *>(row + p);
+        out[0] = t.x; out[1] = t.y; out[2] = t.z; out[3] = t.w;
+    };
+    float h[9][4];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const float *row = sb + i * SEG;
+        const bool bb = Y.wall[1 - L::ey(i)];
+        const int s = bb ? 0 : -L::ex(i);
+        float B[4];
+        v4(row, x0l + 4, B);
+        if (s == 0) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) h[i][c] = B[c];
+        } else if (s < 0) {
+            float A[4];
+            v4(row, x0l, A);
+            h[i][0] = A[3]; h[i][1] = B[0]; h[i][2] = B[1]; h[i][3] = B[2];
+        } else {
+            float C[4];
+            v4(row, x0l + 8, C);
+            h[i][0] = B[1]; h[i][1] = B[2]; h[i][2] = B[3]; h[i][3] = C[0];
+        }
+    }
+    // eps rows y-1, y, y+1 at columns x0-1 .. x0+4
+    float E[3][6];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        float A[4], B[4], C[4];
+        v4(ey_slot[r], x0l, A);
+        v4(ey_slot[r], x0l + 4, B);
+        v4(ey_slot[r], x0l + 8, C);
+        E[r][0] = A[3];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) E[r][c + 1] = B[c];
+        E[r][5] = C[0];
+    }
+    float out[9][4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        float hh[9], et[9], o[9];
+        const float e0 = E[1][c + 1];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            hh[i] = h[i][c];
+            const bool wall = Y.wall[1 + L::ey(i)];
+            et[i] = (i == 0 || wall) ? e0 : E[1 + L::ey(i)][c + 1 + L::ex(i)];
+        }
+        apply_moving_wall<9>(d, Y.wall[2], Z, e0, hh);
+        collide<9>(d, hh, e0, et, o);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) out[i][c] = o[i];
+    }
+    const int x0 = xs + x0l;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) st_masked<4>(fout + i * d.plane + ro, x0, d.nx, out[i]);
+    if (x0 == 0) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            if (L::ex(i) < 0) fout[i * d.plane + ro + d.nx] = out[i][0];
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        if (x0 + c == d.nx - 1) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i)
+                if (L::ex(i) > 0) fout[i * d.plane + ro - 1] = out[i][c];
+        }
+    }
+}
+
 // One strip of tiles: column block starting at xs, plane z, rows [y0, y1).
-template <int Q, int NT, int CPT>
+// VEC (D2Q9, CPT = 4): the contiguous 4-cells-per-thread compute above.
+template <int Q, int NT, int CPT, bool VEC = false>
 __device__ __forceinline__ void ring_strip(const VDom &d, const float *__restrict__ fin,
                                            float *__restrict__ fout, int xs, int z, int y0, int y1,
                                            int stages, unsigned char *smem) {
@@ -277,6 +363,9 @@ __device__ __forceinline__ void ring_strip(const VDom &d, const float *__restric
         const int y = y0 + k;
         const Nb3 Y = nb3<true>(y, d.ny, d.wall_y);
         const long long ro = row_offset(d, y, z);
+        if constexpr (VEC) {
+            ring_tile_vec9<NT>(d, sb, ey_slot, Y, Z, fout, ro, xs, tid);
+        } else {
 #pragma unroll
         for (int cc = 0; cc < CPT; ++cc) {
             const int xl = tid + cc * NT;
@@ -312,6 +401,7 @@ __device__ __forceinline__ void ring_strip(const VDom &d, const float *__restric
                 }
             }
         }
+        }
         __syncthreads();
         if (tid == 0 && k + stages < n) {
             fence_proxy_async_smem();
@@ -331,7 +421,7 @@ __device__ __forceinline__ void ring_strip(const VDom &d, const float *__restric
     }
 }
 
-template <int Q, int NT, int CPT>
+template <int Q, int NT, int CPT, bool VEC = false>
 __global__ void __launch_bounds__(NT) k_step_tma_ring(const VDom d, const float *__restrict__ fin,
                                                       float *__restrict__ fout, int ntx, int per_y,
                                                       int stages) {
@@ -343,7 +433,7 @@ __global__ void __launch_bounds__(NT) k_step_tma_ring(const VDom d, const float 
     const int yc = rem / d.nz;
     const int y0 = (int)((long long)yc * d.ny / per_y);
     const int y1 = (int)((long long)(yc + 1) * d.ny / per_y);
-    ring_strip<Q, NT, CPT>(d, fin, fout, xt * NT * CPT, z, y0, y1, stages, smem);
+    ring_strip<Q, NT, CPT, VEC>(d, fin, fout, xt * NT * CPT, z, y0, y1, stages, smem);
 }
 
 // Batched D2Q9: CTA b takes strip b of a table built on the host (domain,
@@ -380,7 +470,7 @@ static int pick_per_y(int ncol, int ny, long long resident) {
     return best;
 }
 
-template <int Q, int NT, int CPT>
+template <int Q, int NT, int CPT, bool VEC = false>
 static cudaError_t launch_ring_t(const VDom &d, const float *fin, float *fout, int stages,
                                  cudaStream_t stream) {
     constexpr int TW = NT * CPT;
@@ -388,7 +478,7 @@ static cudaError_t launch_ring_t(const VDom &d, const float *fin, float *fout, i
     const size_t smem =
         kBarBytes + (size_t)(stages * Q + (stages + 2) * NZR) * (TW + 8) * sizeof(float);
     if (stages < 2 || stages > 16 || smem > 227 * 1024) return cudaErrorInvalidValue;
-    auto kern = k_step_tma_ring<Q, NT, CPT>;
+    auto kern = k_step_tma_ring<Q, NT, CPT, VEC>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, occ = 0;
@@ -465,6 +555,12 @@ cudaError_t launch_ring_batched(const VDom *doms, const Tile *strips, int nstrip
 cudaError_t launch_step_tma(int q, const VDom &d, const float *fin, float *fout, Launch L,
                             cudaStream_t stream) {
     const int nt = 32 * L.warps;
+    if (L.kind == 3) {       // ring pipeline, 4 consecutive cells per thread (D2Q9)
+        if (q != 9 || L.cpt != 4) return cudaErrorInvalidValue;
+        if (nt == 64) return launch_ring_t<9, 64, 4, true>(d, fin, fout, L.rows, stream);
+        if (nt == 128) return launch_ring_t<9, 128, 4, true>(d, fin, fout, L.rows, stream);
+        return cudaErrorInvalidValue;
+    }
     if (L.kind == 2) {
 #define VANS_RING_CASE(QQ, NTT, CC)                              \
         if (q == QQ && nt == NTT && L.cpt == CC)                 \
