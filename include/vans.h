@@ -90,6 +90,9 @@ typedef struct {
  *         shared-memory ring, so each eps row is read from HBM once per strip.
  * kind 3: D2Q9 only: kind 2 with each thread on 4 consecutive cells (cpt 4,
  *         warps 2 or 4): 16-byte shared loads and global stores.
+ * kind 4, 5: kinds 2 and 3 with one extra producer warp per CTA (warps counts
+ *         the compute warps only): stages are released per warp through
+ *         "empty" mbarriers instead of a block-wide barrier per tile.
  *         The batched path takes kinds 0 and 2 (kind 2: one CTA per strip of
  *         up to 32 rows of one domain). */
 typedef struct {

@@ -90,7 +90,9 @@ class Params:
 class Launch:
     """kind 0: register-load kernel (cpt cells per lane, warps x rows per block);
     kind 1: bulk-copy pipeline (32*warps threads, cpt cells per thread per tile,
-    rows = pipeline stages)."""
+    rows = pipeline stages); kind 2: pipeline over row strips with a porosity
+    ring; kind 3: kind 2 with 4 contiguous cells per thread (D2Q9); kinds 4, 5:
+    kinds 2, 3 with a producer warp and per-warp stage release."""
     cpt: int
     warps: int
     rows: int

@@ -110,11 +110,11 @@ bool launch_ok(const vans_launch *c, int q, bool batched) {
         if (c->warps < 1 || c->warps > 8 || c->rows < 1 || c->rows > 8) return false;
         return c->warps * c->rows <= 8;
     }
-    if (c->kind < 1 || c->kind > 3 || (batched && c->kind != 2)) return false;
+    if (c->kind < 1 || c->kind > 5 || (batched && c->kind != 2)) return false;
     if (c->rows < 2 || c->rows > 6) return false;
     // the instantiated pipeline shapes
     const int nt = 32 * c->warps;
-    if (c->kind == 3) return q == 9 && c->cpt == 4 && (nt == 64 || nt == 128);
+    if (c->kind == 3 || c->kind == 5) return q == 9 && c->cpt == 4 && (nt == 64 || nt == 128);
     if (q == 9)
         return (nt == 128 && (c->cpt == 2 || c->cpt == 4)) || (nt == 256 && c->cpt <= 2);
     return (nt == 128 && c->cpt <= 2) || (nt == 256 && c->cpt == 1);
@@ -344,19 +344,22 @@ std::vector<Launch> candidates(int q, bool batched) {
         c.insert(c.end(), t, t + 6);
         return c;
     }
-    // bulk-copy pipeline shapes {cpt, warps, stages, 1}
+    // bulk-copy pipeline shapes {cpt, warps, stages, kind}
     if (q == 9) {
         const Launch t[] = {{2, 4, 3, 1}, {2, 4, 4, 1}, {4, 4, 2, 1}, {4, 4, 3, 1},
                             {1, 8, 3, 1}, {1, 8, 4, 1}, {2, 8, 2, 1}, {2, 8, 3, 1},
                             {2, 4, 3, 2}, {2, 4, 4, 2}, {4, 4, 3, 2}, {1, 8, 3, 2},
                             {1, 8, 4, 2}, {2, 8, 3, 2}, {4, 4, 2, 3}, {4, 4, 3, 3},
-                            {4, 2, 3, 3}, {4, 2, 4, 3}};
-        c.insert(c.end(), t, t + 18);
+                            {4, 2, 3, 3}, {4, 2, 4, 3}, {2, 8, 2, 4}, {4, 4, 2, 4},
+                            {4, 2, 2, 5}, {4, 4, 2, 5}, {4, 4, 4, 5}, {4, 4, 5, 5},
+                            {4, 4, 6, 5}};
+        c.insert(c.end(), t, t + 25);
     } else {
         const Launch t[] = {{1, 4, 3, 1}, {1, 4, 4, 1}, {2, 4, 2, 1}, {2, 4, 3, 1},
                             {1, 8, 2, 1}, {1, 8, 3, 1}, {1, 4, 3, 2}, {2, 4, 2, 2},
-                            {2, 4, 3, 2}, {1, 8, 2, 2}, {1, 8, 3, 2}};
-        c.insert(c.end(), t, t + 11);
+                            {2, 4, 3, 2}, {1, 8, 2, 2}, {1, 8, 3, 2}, {1, 4, 3, 4},
+                            {1, 8, 2, 4}};
+        c.insert(c.end(), t, t + 13);
     }
     return c;
 }

@@ -314,58 +314,16 @@ __device__ __forceinline__ void ring_tile_vec9(const VDom &d, const float *__res
     }
 }
 
-// One strip of tiles: column block starting at xs, plane z, rows [y0, y1).
-// VEC (D2Q9, CPT = 4): the contiguous 4-cells-per-thread compute above.
-template <int Q, int NT, int CPT, bool VEC = false>
-__device__ __forceinline__ void ring_strip(const VDom &d, const float *__restrict__ fin,
-                                           float *__restrict__ fout, int xs, int z, int y0, int y1,
-                                           int stages, unsigned char *smem) {
+// Compute and store one staged tile of the ring pipeline (all NT threads).
+template <int Q, int NT, int CPT, bool VEC>
+__device__ __forceinline__ void ring_tile(const VDom &d, const float *__restrict__ sb,
+                                          const float *const ey_slot[3], const Nb3 &Y, const Nb3 &Z,
+                                          float *__restrict__ fout, long long ro, int xs, int tid) {
     using L = Lat<Q>;
-    constexpr int TW = NT * CPT;
-    constexpr int SEG = TW + 8;
-    constexpr int NZR = (Q == 9) ? 1 : 3;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
-    float *buf = reinterpret_cast<float *>(smem + kBarBytes);
-    float *ring = buf + stages * Q * SEG;
-    const int rslots = stages + 2;
-    const int tid = threadIdx.x;
-    const int n = y1 - y0;
-    if (n <= 0) return;
-
-    if (tid == 0) {
-        for (int s = 0; s < stages; ++s) mbar_init(&bars[s], 1);
-        mbar_init_fence();
-    }
-    __syncthreads();
-    if (tid == 0) {
-        const int pre = n < stages ? n : stages;
-        for (int k = 0; k < pre; ++k)
-            issue_tile_ring<Q, TW>(d, fin, y0 + k, z, xs, k, y0, buf + k * Q * SEG, ring, rslots,
-                                   &bars[k]);
-    }
-    Nb3 Z;
-    if (Q == 19) {
-        Z = nb3<true>(z, d.nz, d.wall_z);
+    constexpr int SEG = NT * CPT + 8;
+    if constexpr (VEC) {
+        ring_tile_vec9<NT>(d, sb, ey_slot, Y, Z, fout, ro, xs, tid);
     } else {
-        Z.r[0] = Z.r[1] = Z.r[2] = 0;
-        Z.wall[0] = Z.wall[1] = Z.wall[2] = false;
-    }
-    int k = 0, s = 0;
-    uint32_t par = 0;
-    bool ok = true;
-    for (; k < n; ++k) {
-        ok = __syncthreads_and(mbar_wait_bounded(&bars[s], par));
-        if (!ok) break;
-        const float *sb = buf + s * Q * SEG;
-        const float *ey_slot[3] = {ring + (k % rslots) * (NZR * SEG),          // y-1
-                                   ring + ((k + 1) % rslots) * (NZR * SEG),    // y
-                                   ring + ((k + 2) % rslots) * (NZR * SEG)};   // y+1
-        const int y = y0 + k;
-        const Nb3 Y = nb3<true>(y, d.ny, d.wall_y);
-        const long long ro = row_offset(d, y, z);
-        if constexpr (VEC) {
-            ring_tile_vec9<NT>(d, sb, ey_slot, Y, Z, fout, ro, xs, tid);
-        } else {
 #pragma unroll
         for (int cc = 0; cc < CPT; ++cc) {
             const int xl = tid + cc * NT;
@@ -401,7 +359,64 @@ __device__ __forceinline__ void ring_strip(const VDom &d, const float *__restric
                 }
             }
         }
-        }
+    }
+}
+
+template <int Q>
+__device__ __forceinline__ Nb3 plane_nbs(const VDom &d, int z) {
+    Nb3 Z;
+    if (Q == 19) {
+        Z = nb3<true>(z, d.nz, d.wall_z);
+    } else {
+        Z.r[0] = Z.r[1] = Z.r[2] = 0;
+        Z.wall[0] = Z.wall[1] = Z.wall[2] = false;
+    }
+    return Z;
+}
+
+// One strip of tiles: column block starting at xs, plane z, rows [y0, y1).
+// VEC (D2Q9, CPT = 4): the contiguous 4-cells-per-thread compute above.
+// Thread 0 refills a stage after a CTA barrier says every thread is done with it.
+template <int Q, int NT, int CPT, bool VEC = false>
+__device__ __forceinline__ void ring_strip(const VDom &d, const float *__restrict__ fin,
+                                           float *__restrict__ fout, int xs, int z, int y0, int y1,
+                                           int stages, unsigned char *smem) {
+    constexpr int TW = NT * CPT;
+    constexpr int SEG = TW + 8;
+    constexpr int NZR = (Q == 9) ? 1 : 3;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
+    float *buf = reinterpret_cast<float *>(smem + kBarBytes);
+    float *ring = buf + stages * Q * SEG;
+    const int rslots = stages + 2;
+    const int tid = threadIdx.x;
+    const int n = y1 - y0;
+    if (n <= 0) return;
+
+    if (tid == 0) {
+        for (int s = 0; s < stages; ++s) mbar_init(&bars[s], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const int pre = n < stages ? n : stages;
+        for (int k = 0; k < pre; ++k)
+            issue_tile_ring<Q, TW>(d, fin, y0 + k, z, xs, k, y0, buf + k * Q * SEG, ring, rslots,
+                                   &bars[k]);
+    }
+    const Nb3 Z = plane_nbs<Q>(d, z);
+    int k = 0, s = 0;
+    uint32_t par = 0;
+    bool ok = true;
+    for (; k < n; ++k) {
+        ok = __syncthreads_and(mbar_wait_bounded(&bars[s], par));
+        if (!ok) break;
+        const float *sb = buf + s * Q * SEG;
+        const float *ey_slot[3] = {ring + (k % rslots) * (NZR * SEG),          // y-1
+                                   ring + ((k + 1) % rslots) * (NZR * SEG),    // y
+                                   ring + ((k + 2) % rslots) * (NZR * SEG)};   // y+1
+        const int y = y0 + k;
+        const Nb3 Y = nb3<true>(y, d.ny, d.wall_y);
+        ring_tile<Q, NT, CPT, VEC>(d, sb, ey_slot, Y, Z, fout, row_offset(d, y, z), xs, tid);
         __syncthreads();
         if (tid == 0 && k + stages < n) {
             fence_proxy_async_smem();
@@ -421,10 +436,92 @@ __device__ __forceinline__ void ring_strip(const VDom &d, const float *__restric
     }
 }
 
+// Warp-specialised form of the strip: NT compute threads plus one producer
+// warp.  Stage s has a "full" barrier (the bulk copies' transaction count) and
+// an "empty" barrier that each compute warp arrives on once it has read the
+// stage; lane 0 of the producer warp refills a stage as soon as its empty
+// phase completes.  No CTA-wide barrier sits in the loop, so a compute warp
+// that finishes a tile moves on to the next staged one without waiting for the
+// others.  Stage reuse is the same as above: tile k+stages (and the eps ring
+// slot it loads, last read by tile k) is issued after every warp is done with
+// tile k.  stages <= kBarBytes / 16.
 template <int Q, int NT, int CPT, bool VEC = false>
-__global__ void __launch_bounds__(NT) k_step_tma_ring(const VDom d, const float *__restrict__ fin,
-                                                      float *__restrict__ fout, int ntx, int per_y,
-                                                      int stages) {
+__device__ __forceinline__ void ring_strip_ws(const VDom &d, const float *__restrict__ fin,
+                                              float *__restrict__ fout, int xs, int z, int y0, int y1,
+                                              int stages, unsigned char *smem) {
+    constexpr int TW = NT * CPT;
+    constexpr int SEG = TW + 8;
+    constexpr int NZR = (Q == 9) ? 1 : 3;
+    constexpr int NCW = NT / 32;          // compute warps
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
+    uint64_t *empty = full + stages;
+    float *buf = reinterpret_cast<float *>(smem + kBarBytes);
+    float *ring = buf + stages * Q * SEG;
+    const int rslots = stages + 2;
+    const int tid = threadIdx.x;
+    const int n = y1 - y0;
+    if (n <= 0) return;
+
+    if (tid == 0) {
+        for (int s = 0; s < stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], NCW);
+        }
+        mbar_init_fence();
+    }
+    __syncthreads();
+    if (tid >= NT) {                      // producer warp
+        if (tid != NT) return;
+        int issued = 0;
+        bool ok = true;
+        for (int k = 0; k < n; ++k) {
+            const int s = k % stages;
+            if (k >= stages) {
+                ok = mbar_wait_bounded(&empty[s], (uint32_t)(((k / stages) - 1) & 1));
+                if (!ok) break;
+                fence_proxy_async_smem();
+            }
+            issue_tile_ring<Q, TW>(d, fin, y0 + k, z, xs, k, y0, buf + s * Q * SEG, ring, rslots,
+                                   &full[s]);
+            issued = k + 1;
+        }
+        if (!ok) {
+            // a compute warp gave up: flag it and let the copies in flight land
+            // before the CTA's shared memory goes away
+            if (d.status) atomicOr(d.status, 2);
+            const int first = issued > stages ? issued - stages : 0;
+            for (int j = first; j < issued; ++j)
+                mbar_wait_bounded(&full[j % stages], (uint32_t)((j / stages) & 1));
+        }
+        return;
+    }
+    const int lane = tid & 31;
+    const Nb3 Z = plane_nbs<Q>(d, z);
+    int s = 0;
+    uint32_t par = 0;
+    for (int k = 0; k < n; ++k) {
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[s], par))) {
+            if (lane == 0 && d.status) atomicOr(d.status, 2);
+            return;
+        }
+        const float *sb = buf + s * Q * SEG;
+        const float *ey_slot[3] = {ring + (k % rslots) * (NZR * SEG),
+                                   ring + ((k + 1) % rslots) * (NZR * SEG),
+                                   ring + ((k + 2) % rslots) * (NZR * SEG)};
+        const int y = y0 + k;
+        const Nb3 Y = nb3<true>(y, d.ny, d.wall_y);
+        ring_tile<Q, NT, CPT, VEC>(d, sb, ey_slot, Y, Z, fout, row_offset(d, y, z), xs, tid);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+        if (++s == stages) { s = 0; par ^= 1u; }
+    }
+}
+
+template <int Q, int NT, int CPT, bool VEC = false, bool WS = false>
+__global__ void __launch_bounds__(WS ? NT + 32 : NT) k_step_tma_ring(const VDom d,
+                                                                      const float *__restrict__ fin,
+                                                                      float *__restrict__ fout,
+                                                                      int ntx, int per_y, int stages) {
     extern __shared__ __align__(128) unsigned char smem[];
     // strip of this CTA: column block xt, plane z, rows [y0, y1)
     const int xt = blockIdx.x % ntx;
@@ -433,7 +530,10 @@ __global__ void __launch_bounds__(NT) k_step_tma_ring(const VDom d, const float 
     const int yc = rem / d.nz;
     const int y0 = (int)((long long)yc * d.ny / per_y);
     const int y1 = (int)((long long)(yc + 1) * d.ny / per_y);
-    ring_strip<Q, NT, CPT, VEC>(d, fin, fout, xt * NT * CPT, z, y0, y1, stages, smem);
+    if constexpr (WS)
+        ring_strip_ws<Q, NT, CPT, VEC>(d, fin, fout, xt * NT * CPT, z, y0, y1, stages, smem);
+    else
+        ring_strip<Q, NT, CPT, VEC>(d, fin, fout, xt * NT * CPT, z, y0, y1, stages, smem);
 }
 
 // Batched D2Q9: CTA b takes strip b of a table built on the host (domain,
@@ -470,21 +570,23 @@ static int pick_per_y(int ncol, int ny, long long resident) {
     return best;
 }
 
-template <int Q, int NT, int CPT, bool VEC = false>
+template <int Q, int NT, int CPT, bool VEC = false, bool WS = false>
 static cudaError_t launch_ring_t(const VDom &d, const float *fin, float *fout, int stages,
                                  cudaStream_t stream) {
     constexpr int TW = NT * CPT;
     constexpr int NZR = (Q == 9) ? 1 : 3;
     const size_t smem =
         kBarBytes + (size_t)(stages * Q + (stages + 2) * NZR) * (TW + 8) * sizeof(float);
-    if (stages < 2 || stages > 16 || smem > 227 * 1024) return cudaErrorInvalidValue;
-    auto kern = k_step_tma_ring<Q, NT, CPT, VEC>;
+    const int max_stages = WS ? kBarBytes / 16 : kBarBytes / 8;
+    if (stages < 2 || stages > max_stages || smem > 227 * 1024) return cudaErrorInvalidValue;
+    auto kern = k_step_tma_ring<Q, NT, CPT, VEC, WS>;
+    constexpr int nthreads = WS ? NT + 32 : NT;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, occ = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, nthreads, smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     const int ntx = (d.nx + TW - 1) / TW;
@@ -492,7 +594,7 @@ static cudaError_t launch_ring_t(const VDom &d, const float *fin, float *fout, i
     const int per_y = pick_per_y(ncol, d.ny, (long long)sms * occ);
     const long long grid = (long long)ncol * per_y;
     if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    kern<<<(unsigned)grid, NT, smem, stream>>>(d, fin, fout, ntx, per_y, stages);
+    kern<<<(unsigned)grid, nthreads, smem, stream>>>(d, fin, fout, ntx, per_y, stages);
     return cudaGetLastError();
 }
 
@@ -550,21 +652,30 @@ cudaError_t launch_ring_batched(const VDom *doms, const Tile *strips, int nstrip
     return cudaErrorInvalidValue;
 }
 
-// L.warps -> threads per CTA (32 * warps), L.cpt -> cells per thread per tile,
-// L.rows -> pipeline stages; kind 2 selects the D2Q9 porosity-ring variant
+// L.warps -> compute threads per CTA (32 * warps), L.cpt -> cells per thread
+// per tile, L.rows -> pipeline stages; kind 1 the plain pipeline, 2 the
+// porosity ring, 3 the ring with contiguous cells (D2Q9), 4 and 5 the
+// warp-specialised forms of 2 and 3 (one extra producer warp)
 cudaError_t launch_step_tma(int q, const VDom &d, const float *fin, float *fout, Launch L,
                             cudaStream_t stream) {
     const int nt = 32 * L.warps;
-    if (L.kind == 3) {       // ring pipeline, 4 consecutive cells per thread (D2Q9)
+    if (L.kind == 3 || L.kind == 5) {   // ring pipeline, 4 consecutive cells per thread (D2Q9)
         if (q != 9 || L.cpt != 4) return cudaErrorInvalidValue;
-        if (nt == 64) return launch_ring_t<9, 64, 4, true>(d, fin, fout, L.rows, stream);
-        if (nt == 128) return launch_ring_t<9, 128, 4, true>(d, fin, fout, L.rows, stream);
+        const bool ws = L.kind == 5;
+        if (nt == 64)
+            return ws ? launch_ring_t<9, 64, 4, true, true>(d, fin, fout, L.rows, stream)
+                      : launch_ring_t<9, 64, 4, true>(d, fin, fout, L.rows, stream);
+        if (nt == 128)
+            return ws ? launch_ring_t<9, 128, 4, true, true>(d, fin, fout, L.rows, stream)
+                      : launch_ring_t<9, 128, 4, true>(d, fin, fout, L.rows, stream);
         return cudaErrorInvalidValue;
     }
-    if (L.kind == 2) {
-#define VANS_RING_CASE(QQ, NTT, CC)                              \
-        if (q == QQ && nt == NTT && L.cpt == CC)                 \
-            return launch_ring_t<QQ, NTT, CC>(d, fin, fout, L.rows, stream);
+    if (L.kind == 2 || L.kind == 4) {
+        const bool ws = L.kind == 4;
+#define VANS_RING_CASE(QQ, NTT, CC)                                                     \
+        if (q == QQ && nt == NTT && L.cpt == CC)                                        \
+            return ws ? launch_ring_t<QQ, NTT, CC, false, true>(d, fin, fout, L.rows, stream) \
+                      : launch_ring_t<QQ, NTT, CC>(d, fin, fout, L.rows, stream);
         VANS_RING_CASE(9, 128, 2)
         VANS_RING_CASE(9, 128, 4)
         VANS_RING_CASE(9, 256, 1)
