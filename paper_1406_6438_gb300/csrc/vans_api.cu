@@ -110,7 +110,7 @@ bool launch_ok(const vans_launch *c, int q, bool batched) {
         if (c->warps < 1 || c->warps > 8 || c->rows < 1 || c->rows > 8) return false;
         return c->warps * c->rows <= 8;
     }
-    if (c->kind < 1 || c->kind > 5 || (batched && c->kind != 2)) return false;
+    if (c->kind < 1 || c->kind > 5 || (batched && c->kind != 2 && c->kind < 4)) return false;
     if (c->rows < 2 || c->rows > 6) return false;
     // the instantiated pipeline shapes
     const int nt = 32 * c->warps;
@@ -176,13 +176,17 @@ void drop_graph(vans_t h) {
     h->seg_graphs.clear();
 }
 
+// one batched step with the handle's launch (strip kernels for kinds 2, 4, 5)
+cudaError_t batched_step(vans_t h, cudaStream_t s, int par) {
+    if (h->L.kind != 0)
+        return vans::launch_ring_batched(h->doms_d, h->tiles_d, (int)h->tiles.size(), par, h->L, s);
+    return vans::launch_step_batched(h->doms_d, h->tiles_d, (int)h->tiles.size(), par, h->L,
+                                     h->grid, s);
+}
+
 cudaError_t one_step(vans_t h, cudaStream_t s, int par) {
     ++h->launches;
-    if (h->batched && h->L.kind == 2)
-        return vans::launch_ring_batched(h->doms_d, h->tiles_d, (int)h->tiles.size(), par, h->L, s);
-    if (h->batched)
-        return vans::launch_step_batched(h->doms_d, h->tiles_d, (int)h->tiles.size(), par, h->L,
-                                         h->grid, s);
+    if (h->batched) return batched_step(h, s, par);
     return vans::launch_step(h->q, h->dom, h->st[par], h->st[par ^ 1], h->L, s);
 }
 
@@ -261,7 +265,7 @@ constexpr int kStripRows = 32;   // rows per strip of the batched pipeline kerne
 void build_tiles(vans_t h, const Launch &L, std::vector<Tile> &out) {
     out.clear();
     const int bx = 32 * L.cpt * L.warps;
-    if (L.kind == 2) {
+    if (L.kind != 0) {
         // strips of up to kStripRows rows per column block, largest first so the
         // last wave of CTAs holds the short ones
         for (int d = 0; d < h->n; ++d) {
@@ -340,8 +344,9 @@ std::vector<Launch> candidates(int q, bool batched) {
             }
     if (batched) {
         const Launch t[] = {{2, 4, 3, 2}, {4, 4, 2, 2}, {4, 4, 3, 2}, {2, 8, 2, 2}, {2, 8, 3, 2},
-                            {1, 8, 3, 2}};
-        c.insert(c.end(), t, t + 6);
+                            {1, 8, 3, 2}, {2, 8, 2, 4}, {2, 4, 2, 4}, {4, 2, 2, 5}, {4, 2, 3, 5},
+                            {4, 4, 2, 5}, {4, 4, 3, 5}, {4, 4, 4, 5}};
+        c.insert(c.end(), t, t + 13);
         return c;
     }
     // bulk-copy pipeline shapes {cpt, warps, stages, kind}
@@ -880,13 +885,7 @@ int vans_batch_autotune(vans_t h, vans_launch *chosen) {
     for (const Launch &L : candidates(9, true)) {
         if (set_batch_launch(h, L) != VANS_OK) continue;
         // reads the current parity and writes the other buffer of every domain
-        const float ms = time_launches(
-            h,
-            [&] {
-                vans::launch_step_batched(h->doms_d, h->tiles_d, (int)h->tiles.size(), par, h->L,
-                                          h->grid, h->stream);
-            },
-            5);
+        const float ms = time_launches(h, [&] { batched_step(h, h->stream, par); }, 5);
         h->launches += 17;
         if (ms < best_ms) {
             best_ms = ms;

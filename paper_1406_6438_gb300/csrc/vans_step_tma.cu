@@ -539,16 +539,18 @@ __global__ void __launch_bounds__(WS ? NT + 32 : NT) k_step_tma_ring(const VDom 
 // Batched D2Q9: CTA b takes strip b of a table built on the host (domain,
 // column block, rows y0..y1-1; largest strips first) and advances it with the
 // porosity-ring pipeline, using that domain's descriptor and buffers.
-template <int NT, int CPT>
-__global__ void __launch_bounds__(NT) k_step_ring_batched(const VDom *__restrict__ doms,
-                                                          const Tile *__restrict__ strips, int parity,
-                                                          int stages) {
+template <int NT, int CPT, bool VEC = false, bool WS = false>
+__global__ void __launch_bounds__(WS ? NT + 32 : NT) k_step_ring_batched(
+    const VDom *__restrict__ doms, const Tile *__restrict__ strips, int parity, int stages) {
     extern __shared__ __align__(128) unsigned char smem[];
     const Tile S = strips[blockIdx.x];   // {dom, y0, x0, y1}
     const VDom d = doms[S.dom];
     const float *fin = parity ? d.f[1] : d.f[0];
     float *fout = parity ? d.f[0] : d.f[1];
-    ring_strip<9, NT, CPT>(d, fin, fout, S.x0, 0, S.row, S.pad, stages, smem);
+    if constexpr (WS)
+        ring_strip_ws<9, NT, CPT, VEC>(d, fin, fout, S.x0, 0, S.row, S.pad, stages, smem);
+    else
+        ring_strip<9, NT, CPT, VEC>(d, fin, fout, S.x0, 0, S.row, S.pad, stages, smem);
 }
 
 // Strips per (column block, plane): the smallest count whose grid fills the
@@ -629,26 +631,46 @@ static cudaError_t launch_tma_t(const VDom &d, const float *fin, float *fout, in
     return cudaGetLastError();
 }
 
-template <int NT, int CPT>
+template <int NT, int CPT, bool VEC = false, bool WS = false>
 static cudaError_t launch_ring_batched_t(const VDom *doms, const Tile *strips, int nstrips, int parity,
                                          int stages, cudaStream_t stream) {
     constexpr int TW = NT * CPT;
     const size_t smem = kBarBytes + (size_t)(stages * 9 + (stages + 2)) * (TW + 8) * sizeof(float);
-    if (stages < 2 || stages > 16 || smem > 227 * 1024 || nstrips < 1) return cudaErrorInvalidValue;
-    auto kern = k_step_ring_batched<NT, CPT>;
+    const int max_stages = WS ? kBarBytes / 16 : kBarBytes / 8;
+    if (stages < 2 || stages > max_stages || smem > 227 * 1024 || nstrips < 1)
+        return cudaErrorInvalidValue;
+    auto kern = k_step_ring_batched<NT, CPT, VEC, WS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<nstrips, NT, smem, stream>>>(doms, strips, parity, stages);
+    kern<<<nstrips, WS ? NT + 32 : NT, smem, stream>>>(doms, strips, parity, stages);
     return cudaGetLastError();
 }
 
+// kind 2: ring strips; 4: the same, warp-specialised; 5: warp-specialised with
+// 4 contiguous cells per thread
 cudaError_t launch_ring_batched(const VDom *doms, const Tile *strips, int nstrips, int parity,
                                 Launch L, cudaStream_t stream) {
     const int nt = 32 * L.warps;
-    if (nt == 128 && L.cpt == 2) return launch_ring_batched_t<128, 2>(doms, strips, nstrips, parity, L.rows, stream);
-    if (nt == 128 && L.cpt == 4) return launch_ring_batched_t<128, 4>(doms, strips, nstrips, parity, L.rows, stream);
-    if (nt == 256 && L.cpt == 1) return launch_ring_batched_t<256, 1>(doms, strips, nstrips, parity, L.rows, stream);
-    if (nt == 256 && L.cpt == 2) return launch_ring_batched_t<256, 2>(doms, strips, nstrips, parity, L.rows, stream);
+    const int st = L.rows;
+    if (L.kind == 5) {
+        if (nt == 64 && L.cpt == 4)
+            return launch_ring_batched_t<64, 4, true, true>(doms, strips, nstrips, parity, st, stream);
+        if (nt == 128 && L.cpt == 4)
+            return launch_ring_batched_t<128, 4, true, true>(doms, strips, nstrips, parity, st, stream);
+        return cudaErrorInvalidValue;
+    }
+    if (L.kind != 2 && L.kind != 4) return cudaErrorInvalidValue;
+    const bool ws = L.kind == 4;
+#define VANS_RB_CASE(NTT, CC)                                                                   \
+    if (nt == NTT && L.cpt == CC)                                                               \
+        return ws ? launch_ring_batched_t<NTT, CC, false, true>(doms, strips, nstrips, parity, st, \
+                                                               stream)                        \
+                  : launch_ring_batched_t<NTT, CC>(doms, strips, nstrips, parity, st, stream);
+    VANS_RB_CASE(128, 2)
+    VANS_RB_CASE(128, 4)
+    VANS_RB_CASE(256, 1)
+    VANS_RB_CASE(256, 2)
+#undef VANS_RB_CASE
     return cudaErrorInvalidValue;
 }
 
