@@ -209,6 +209,7 @@ __device__ __forceinline__ void issue_tile_ring(const VDom &d, const float *__re
     const uint32_t bytes = (uint32_t)((((nval + 3) & ~3) + 8) * 4);
     const int jfirst = (k == 0) ? 0 : k + 2;
     mbar_arrive_expect_tx(bar, bytes * (Q + NZR * (k + 3 - jfirst)));
+    const uint64_t again = l2_evict_last();
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int ey = L::ey(i), ez = L::ez(i);
@@ -224,7 +225,8 @@ __device__ __forceinline__ void issue_tile_ring(const VDom &d, const float *__re
 #pragma unroll
         for (int dz = 0; dz < NZR; ++dz) {
             const int rz = (Q == 9) ? 0 : Z.r[dz];
-            bulk_g2s(slot + dz * SEG, d.eps + row_offset(d, ry, rz) + xs - 4, bytes, bar);
+            bulk_g2s_hint(slot + dz * SEG, d.eps + row_offset(d, ry, rz) + xs - 4, bytes, bar,
+                          again);
         }
     }
 }
@@ -234,11 +236,11 @@ __device__ __forceinline__ void issue_tile_ring(const VDom &d, const float *__re
 // aligned 16-byte shared loads and each output plane leaves in one 16-byte
 // global store, a quarter of the load/store instructions of the strided
 // mapping.  Segment position p holds column xs - 4 + p.
-template <int NT>
+template <int NT, class Rel>
 __device__ __forceinline__ void ring_tile_vec9(const VDom &d, const float *__restrict__ sb,
                                                const float *const ey_slot[3], const Nb3 &Y,
                                                const Nb3 &Z, float *__restrict__ fout, long long ro,
-                                               int xs, int tid) {
+                                               int xs, int tid, Rel &&release) {
     using L = Lat<9>;
     constexpr int SEG = NT * 4 + 8;
     const int x0l = 4 * tid;
@@ -280,6 +282,7 @@ __device__ __forceinline__ void ring_tile_vec9(const VDom &d, const float *__res
         for (int c = 0; c < 4; ++c) E[r][c + 1] = B[c];
         E[r][5] = C[0];
     }
+    release();                  // the stage is no longer read
     float out[9][4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
@@ -315,35 +318,45 @@ __device__ __forceinline__ void ring_tile_vec9(const VDom &d, const float *__res
 }
 
 // Compute and store one staged tile of the ring pipeline (all NT threads).
-template <int Q, int NT, int CPT, bool VEC>
+// Every shared-memory read of the tile comes first, into registers; then
+// release() (the caller's way to hand the stage back to the producer), then
+// the collisions and the global stores.
+template <int Q, int NT, int CPT, bool VEC, class Rel>
 __device__ __forceinline__ void ring_tile(const VDom &d, const float *__restrict__ sb,
                                           const float *const ey_slot[3], const Nb3 &Y, const Nb3 &Z,
-                                          float *__restrict__ fout, long long ro, int xs, int tid) {
+                                          float *__restrict__ fout, long long ro, int xs, int tid,
+                                          Rel &&release) {
     using L = Lat<Q>;
     constexpr int SEG = NT * CPT + 8;
     if constexpr (VEC) {
-        ring_tile_vec9<NT>(d, sb, ey_slot, Y, Z, fout, ro, xs, tid);
+        ring_tile_vec9<NT>(d, sb, ey_slot, Y, Z, fout, ro, xs, tid, release);
     } else {
+        float h[CPT][Q], et[CPT][Q];
 #pragma unroll
         for (int cc = 0; cc < CPT; ++cc) {
             const int xl = tid + cc * NT;
-            const int x = xs + xl;
-            float h[Q], et[Q], o[Q];
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 const bool bb = Y.wall[1 - L::ey(i)] || Z.wall[1 - L::ez(i)];
-                h[i] = sb[i * SEG + 4 + xl + (bb ? 0 : -L::ex(i))];
+                h[cc][i] = sb[i * SEG + 4 + xl + (bb ? 0 : -L::ex(i))];
             }
             const float e0 = ey_slot[1][(Q == 9 ? 0 : 1) * SEG + 4 + xl];
-            et[0] = e0;
+            et[cc][0] = e0;
 #pragma unroll
             for (int i = 1; i < Q; ++i) {
                 const int ey = L::ey(i), ez = L::ez(i);
                 const bool wall = Y.wall[1 + ey] || Z.wall[1 + ez];
-                et[i] = wall ? e0 : ey_slot[1 + ey][(Q == 9 ? 0 : 1 + ez) * SEG + 4 + xl + L::ex(i)];
+                et[cc][i] =
+                    wall ? e0 : ey_slot[1 + ey][(Q == 9 ? 0 : 1 + ez) * SEG + 4 + xl + L::ex(i)];
             }
-            apply_moving_wall<Q>(d, Y.wall[2], Z, e0, h);
-            collide<Q>(d, h, e0, et, o);
+        }
+        release();
+#pragma unroll
+        for (int cc = 0; cc < CPT; ++cc) {
+            const int x = xs + tid + cc * NT;
+            float o[Q];
+            apply_moving_wall<Q>(d, Y.wall[2], Z, et[cc][0], h[cc]);
+            collide<Q>(d, h[cc], et[cc][0], et[cc], o);
             if (x < d.nx) {
 #pragma unroll
                 for (int i = 0; i < Q; ++i) fout[i * d.plane + ro + x] = o[i];
@@ -416,7 +429,8 @@ __device__ __forceinline__ void ring_strip(const VDom &d, const float *__restric
                                    ring + ((k + 2) % rslots) * (NZR * SEG)};   // y+1
         const int y = y0 + k;
         const Nb3 Y = nb3<true>(y, d.ny, d.wall_y);
-        ring_tile<Q, NT, CPT, VEC>(d, sb, ey_slot, Y, Z, fout, row_offset(d, y, z), xs, tid);
+        ring_tile<Q, NT, CPT, VEC>(d, sb, ey_slot, Y, Z, fout, row_offset(d, y, z), xs, tid,
+                                   [] {});
         __syncthreads();
         if (tid == 0 && k + stages < n) {
             fence_proxy_async_smem();
@@ -438,9 +452,10 @@ __device__ __forceinline__ void ring_strip(const VDom &d, const float *__restric
 
 // Warp-specialised form of the strip: NT compute threads plus one producer
 // warp.  Stage s has a "full" barrier (the bulk copies' transaction count) and
-// an "empty" barrier that each compute warp arrives on once it has read the
-// stage; lane 0 of the producer warp refills a stage as soon as its empty
-// phase completes.  No CTA-wide barrier sits in the loop, so a compute warp
+// an "empty" barrier that each compute warp arrives on as soon as its lanes
+// have read the stage into registers (before the collisions and the stores);
+// lane 0 of the producer warp refills a stage as soon as its empty phase
+// completes.  No CTA-wide barrier sits in the loop, so a compute warp
 // that finishes a tile moves on to the next staged one without waiting for the
 // others.  Stage reuse is the same as above: tile k+stages (and the eps ring
 // slot it loads, last read by tile k) is issued after every warp is done with
@@ -510,9 +525,11 @@ __device__ __forceinline__ void ring_strip_ws(const VDom &d, const float *__rest
                                    ring + ((k + 2) % rslots) * (NZR * SEG)};
         const int y = y0 + k;
         const Nb3 Y = nb3<true>(y, d.ny, d.wall_y);
-        ring_tile<Q, NT, CPT, VEC>(d, sb, ey_slot, Y, Z, fout, row_offset(d, y, z), xs, tid);
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[s]);
+        uint64_t *const emp = &empty[s];
+        ring_tile<Q, NT, CPT, VEC>(d, sb, ey_slot, Y, Z, fout, row_offset(d, y, z), xs, tid, [&] {
+            __syncwarp();       // every lane's reads of the stage precede the arrive
+            if (lane == 0) mbar_arrive(emp);
+        });
         if (++s == stages) { s = 0; par ^= 1u; }
     }
 }
