@@ -47,9 +47,10 @@ FALLBACK_HBM_GBS = 6800.0
 TRAFFIC = {
     (4, 4, 3, 2, "2d1a6cde23f6ae50"): 681449984 + 553257984,   # profiles/step_d2q9_ring_4096_full.md
 }
-KERNEL_SOURCES = {0: ("vans_step.cu", "vans_device.cuh"),
-                  1: ("vans_step_tma.cu", "vans_device.cuh", "vans_tma.cuh"),
-                  2: ("vans_step_tma.cu", "vans_device.cuh", "vans_tma.cuh")}
+_PIPELINE_SOURCES = ("vans_step_tma.cu", "vans_device.cuh", "vans_tma.cuh")
+KERNEL_SOURCES = {0: ("vans_step.cu", "vans_device.cuh"), 1: _PIPELINE_SOURCES,
+                  2: _PIPELINE_SOURCES, 3: _PIPELINE_SOURCES, 4: _PIPELINE_SOURCES,
+                  5: _PIPELINE_SOURCES}
 
 
 def kernel_hash(kind: int = 2) -> str:
@@ -61,7 +62,11 @@ def kernel_hash(kind: int = 2) -> str:
     return h.hexdigest()[:16]
 
 
-KERNEL_NAMES = {0: "k_step<9,cpt>", 1: "k_step_tma<9,32*warps,cpt>", 2: "k_step_tma_ring<9,32*warps,cpt>"}
+KERNEL_NAMES = {0: "k_step<9,cpt>", 1: "k_step_tma<9,32*warps,cpt>",
+                2: "k_step_tma_ring<9,32*warps,cpt>",
+                3: "k_step_tma_ring<9,32*warps,4,contiguous>",
+                4: "k_step_tma_ring<9,32*warps,cpt,warp-specialised>",
+                5: "k_step_tma_ring<9,32*warps,4,contiguous,warp-specialised>"}
 
 
 def peaks():

@@ -236,7 +236,7 @@ __device__ __forceinline__ void issue_tile_ring(const VDom &d, const float *__re
 // aligned 16-byte shared loads and each output plane leaves in one 16-byte
 // global store, a quarter of the load/store instructions of the strided
 // mapping.  Segment position p holds column xs - 4 + p.
-template <int NT, class Rel>
+template <int NT, bool EDGE, class Rel>
 __device__ __forceinline__ void ring_tile_vec9(const VDom &d, const float *__restrict__ sb,
                                                const float *const ey_slot[3], const Nb3 &Y,
                                                const Nb3 &Z, float *__restrict__ fout, long long ro,
@@ -244,6 +244,7 @@ __device__ __forceinline__ void ring_tile_vec9(const VDom &d, const float *__res
     using L = Lat<9>;
     constexpr int SEG = NT * 4 + 8;
     const int x0l = 4 * tid;
+    auto ywall = [&](int k) { return EDGE && Y.wall[k]; };
     auto v4 = [&](const float *row, int p, float out[4]) {
         const float4 t = *reinterpret_cast<const float4 *>(row + p);
         out[0] = t.x; out[1] = t.y; out[2] = t.z; out[3] = t.w;
@@ -252,7 +253,7 @@ __device__ __forceinline__ void ring_tile_vec9(const VDom &d, const float *__res
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const float *row = sb + i * SEG;
-        const bool bb = Y.wall[1 - L::ey(i)];
+        const bool bb = ywall(1 - L::ey(i));
         const int s = bb ? 0 : -L::ex(i);
         float B[4];
         v4(row, x0l + 4, B);
@@ -291,10 +292,10 @@ __device__ __forceinline__ void ring_tile_vec9(const VDom &d, const float *__res
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             hh[i] = h[i][c];
-            const bool wall = Y.wall[1 + L::ey(i)];
+            const bool wall = ywall(1 + L::ey(i));
             et[i] = (i == 0 || wall) ? e0 : E[1 + L::ey(i)][c + 1 + L::ex(i)];
         }
-        apply_moving_wall<9>(d, Y.wall[2], Z, e0, hh);
+        if (EDGE) apply_moving_wall<9>(d, Y.wall[2], Z, e0, hh);
         collide<9>(d, hh, e0, et, o);
 #pragma unroll
         for (int i = 0; i < 9; ++i) out[i][c] = o[i];
@@ -321,7 +322,9 @@ __device__ __forceinline__ void ring_tile_vec9(const VDom &d, const float *__res
 // Every shared-memory read of the tile comes first, into registers; then
 // release() (the caller's way to hand the stage back to the producer), then
 // the collisions and the global stores.
-template <int Q, int NT, int CPT, bool VEC, class Rel>
+// EDGE = false: the tile's row touches no wall (the wall flags are known to be
+// false at compile time, which drops the per-direction selects).
+template <int Q, int NT, int CPT, bool VEC, bool EDGE, class Rel>
 __device__ __forceinline__ void ring_tile(const VDom &d, const float *__restrict__ sb,
                                           const float *const ey_slot[3], const Nb3 &Y, const Nb3 &Z,
                                           float *__restrict__ fout, long long ro, int xs, int tid,
@@ -329,15 +332,17 @@ __device__ __forceinline__ void ring_tile(const VDom &d, const float *__restrict
     using L = Lat<Q>;
     constexpr int SEG = NT * CPT + 8;
     if constexpr (VEC) {
-        ring_tile_vec9<NT>(d, sb, ey_slot, Y, Z, fout, ro, xs, tid, release);
+        ring_tile_vec9<NT, EDGE>(d, sb, ey_slot, Y, Z, fout, ro, xs, tid, release);
     } else {
+        auto ywall = [&](int k) { return EDGE && Y.wall[k]; };
+        auto zwall = [&](int k) { return EDGE && Z.wall[k]; };
         float h[CPT][Q], et[CPT][Q];
 #pragma unroll
         for (int cc = 0; cc < CPT; ++cc) {
             const int xl = tid + cc * NT;
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
-                const bool bb = Y.wall[1 - L::ey(i)] || Z.wall[1 - L::ez(i)];
+                const bool bb = ywall(1 - L::ey(i)) || zwall(1 - L::ez(i));
                 h[cc][i] = sb[i * SEG + 4 + xl + (bb ? 0 : -L::ex(i))];
             }
             const float e0 = ey_slot[1][(Q == 9 ? 0 : 1) * SEG + 4 + xl];
@@ -345,7 +350,7 @@ __device__ __forceinline__ void ring_tile(const VDom &d, const float *__restrict
 #pragma unroll
             for (int i = 1; i < Q; ++i) {
                 const int ey = L::ey(i), ez = L::ez(i);
-                const bool wall = Y.wall[1 + ey] || Z.wall[1 + ez];
+                const bool wall = ywall(1 + ey) || zwall(1 + ez);
                 et[cc][i] =
                     wall ? e0 : ey_slot[1 + ey][(Q == 9 ? 0 : 1 + ez) * SEG + 4 + xl + L::ex(i)];
             }
@@ -355,7 +360,7 @@ __device__ __forceinline__ void ring_tile(const VDom &d, const float *__restrict
         for (int cc = 0; cc < CPT; ++cc) {
             const int x = xs + tid + cc * NT;
             float o[Q];
-            apply_moving_wall<Q>(d, Y.wall[2], Z, et[cc][0], h[cc]);
+            if (EDGE) apply_moving_wall<Q>(d, Y.wall[2], Z, et[cc][0], h[cc]);
             collide<Q>(d, h[cc], et[cc][0], et[cc], o);
             if (x < d.nx) {
 #pragma unroll
@@ -417,20 +422,27 @@ __device__ __forceinline__ void ring_strip(const VDom &d, const float *__restric
                                    &bars[k]);
     }
     const Nb3 Z = plane_nbs<Q>(d, z);
-    int k = 0, s = 0;
+    const bool zedge = Z.wall[0] || Z.wall[2];
+    int k = 0, s = 0, j0 = 0;
     uint32_t par = 0;
     bool ok = true;
     for (; k < n; ++k) {
         ok = __syncthreads_and(mbar_wait_bounded(&bars[s], par));
         if (!ok) break;
         const float *sb = buf + s * Q * SEG;
-        const float *ey_slot[3] = {ring + (k % rslots) * (NZR * SEG),          // y-1
-                                   ring + ((k + 1) % rslots) * (NZR * SEG),    // y
-                                   ring + ((k + 2) % rslots) * (NZR * SEG)};   // y+1
+        const int j1 = (j0 + 1 == rslots) ? 0 : j0 + 1, j2 = (j1 + 1 == rslots) ? 0 : j1 + 1;
+        const float *ey_slot[3] = {ring + j0 * (NZR * SEG),    // y-1: ring slot k mod rslots
+                                   ring + j1 * (NZR * SEG),    // y
+                                   ring + j2 * (NZR * SEG)};   // y+1
+        j0 = j1;
         const int y = y0 + k;
         const Nb3 Y = nb3<true>(y, d.ny, d.wall_y);
-        ring_tile<Q, NT, CPT, VEC>(d, sb, ey_slot, Y, Z, fout, row_offset(d, y, z), xs, tid,
-                                   [] {});
+        const long long ro = row_offset(d, y, z);
+        // (D3Q19 keeps one body: a second copy of its larger tile code measured slower)
+        if (Q == 19 || zedge || Y.wall[0] || Y.wall[2])
+            ring_tile<Q, NT, CPT, VEC, true>(d, sb, ey_slot, Y, Z, fout, ro, xs, tid, [] {});
+        else
+            ring_tile<Q, NT, CPT, VEC, false>(d, sb, ey_slot, Y, Z, fout, ro, xs, tid, [] {});
         __syncthreads();
         if (tid == 0 && k + stages < n) {
             fence_proxy_async_smem();
@@ -512,7 +524,8 @@ __device__ __forceinline__ void ring_strip_ws(const VDom &d, const float *__rest
     }
     const int lane = tid & 31;
     const Nb3 Z = plane_nbs<Q>(d, z);
-    int s = 0;
+    const bool zedge = Z.wall[0] || Z.wall[2];
+    int s = 0, j0 = 0;
     uint32_t par = 0;
     for (int k = 0; k < n; ++k) {
         if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[s], par))) {
@@ -520,16 +533,22 @@ __device__ __forceinline__ void ring_strip_ws(const VDom &d, const float *__rest
             return;
         }
         const float *sb = buf + s * Q * SEG;
-        const float *ey_slot[3] = {ring + (k % rslots) * (NZR * SEG),
-                                   ring + ((k + 1) % rslots) * (NZR * SEG),
-                                   ring + ((k + 2) % rslots) * (NZR * SEG)};
+        const int j1 = (j0 + 1 == rslots) ? 0 : j0 + 1, j2 = (j1 + 1 == rslots) ? 0 : j1 + 1;
+        const float *ey_slot[3] = {ring + j0 * (NZR * SEG), ring + j1 * (NZR * SEG),
+                                   ring + j2 * (NZR * SEG)};
+        j0 = j1;
         const int y = y0 + k;
         const Nb3 Y = nb3<true>(y, d.ny, d.wall_y);
+        const long long ro = row_offset(d, y, z);
         uint64_t *const emp = &empty[s];
-        ring_tile<Q, NT, CPT, VEC>(d, sb, ey_slot, Y, Z, fout, row_offset(d, y, z), xs, tid, [&] {
+        auto release = [&] {
             __syncwarp();       // every lane's reads of the stage precede the arrive
             if (lane == 0) mbar_arrive(emp);
-        });
+        };
+        if (Q == 19 || zedge || Y.wall[0] || Y.wall[2])
+            ring_tile<Q, NT, CPT, VEC, true>(d, sb, ey_slot, Y, Z, fout, ro, xs, tid, release);
+        else
+            ring_tile<Q, NT, CPT, VEC, false>(d, sb, ey_slot, Y, Z, fout, ro, xs, tid, release);
         if (++s == stages) { s = 0; par ^= 1u; }
     }
 }
