@@ -88,8 +88,8 @@ typedef struct {
  * kind 2: the kind-1 pipeline where each CTA walks a strip of consecutive rows
  *         (one column block, one z plane) and keeps the porosity rows in a
  *         shared-memory ring, so each eps row is read from HBM once per strip.
- * kind 3: D2Q9 only: kind 2 with each thread on 4 consecutive cells (cpt 4,
- *         warps 2 or 4): 16-byte shared loads and global stores.
+ * kind 3: kind 2 with each thread on consecutive cells (D2Q9: cpt 4, D3Q19:
+ *         cpt 2; warps 2 or 4): 16- or 8-byte shared loads and global stores.
  * kind 4, 5: kinds 2 and 3 with one extra producer warp per CTA (warps counts
  *         the compute warps only): stages are released per warp through
  *         "empty" mbarriers instead of a block-wide barrier per tile.

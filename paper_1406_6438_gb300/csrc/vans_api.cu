@@ -114,7 +114,8 @@ bool launch_ok(const vans_launch *c, int q, bool batched) {
     if (c->rows < 2 || c->rows > 6) return false;
     // the instantiated pipeline shapes
     const int nt = 32 * c->warps;
-    if (c->kind == 3 || c->kind == 5) return q == 9 && c->cpt == 4 && (nt == 64 || nt == 128);
+    if (c->kind == 3 || c->kind == 5)
+        return (nt == 64 || nt == 128) && c->cpt == (q == 9 ? 4 : 2) && (q == 9 || !batched);
     if (q == 9)
         return (nt == 128 && (c->cpt == 2 || c->cpt == 4)) || (nt == 256 && c->cpt <= 2);
     return (nt == 128 && c->cpt <= 2) || (nt == 256 && c->cpt == 1);
@@ -363,8 +364,9 @@ std::vector<Launch> candidates(int q, bool batched) {
         const Launch t[] = {{1, 4, 3, 1}, {1, 4, 4, 1}, {2, 4, 2, 1}, {2, 4, 3, 1},
                             {1, 8, 2, 1}, {1, 8, 3, 1}, {1, 4, 3, 2}, {2, 4, 2, 2},
                             {2, 4, 3, 2}, {1, 8, 2, 2}, {1, 8, 3, 2}, {1, 4, 3, 4},
-                            {1, 8, 2, 4}};
-        c.insert(c.end(), t, t + 13);
+                            {1, 8, 2, 4}, {2, 4, 2, 3}, {2, 4, 3, 3}, {2, 2, 3, 3},
+                            {2, 4, 2, 5}, {2, 4, 3, 5}, {2, 4, 4, 5}, {2, 2, 3, 5}};
+        c.insert(c.end(), t, t + 20);
     }
     return c;
 }

@@ -231,88 +231,112 @@ __device__ __forceinline__ void issue_tile_ring(const VDom &d, const float *__re
     }
 }
 
-// Compute of one staged D2Q9 tile with each thread on 4 consecutive cells
-// (columns x0l..x0l+3 of the tile): each population row comes in one or two
-// aligned 16-byte shared loads and each output plane leaves in one 16-byte
-// global store, a quarter of the load/store instructions of the strided
-// mapping.  Segment position p holds column xs - 4 + p.
-template <int NT, bool EDGE, class Rel>
-__device__ __forceinline__ void ring_tile_vec9(const VDom &d, const float *__restrict__ sb,
-                                               const float *const ey_slot[3], const Nb3 &Y,
-                                               const Nb3 &Z, float *__restrict__ fout, long long ro,
-                                               int xs, int tid, Rel &&release) {
-    using L = Lat<9>;
-    constexpr int SEG = NT * 4 + 8;
-    const int x0l = 4 * tid;
+// Compute of one staged tile with each thread on V consecutive cells (D2Q9:
+// V = 4, D3Q19: V = 2), columns x0l..x0l+V-1 of the tile: each population row
+// comes in one or two aligned V-wide shared loads (8 or 16 bytes) and each
+// output row leaves in one V-wide global store.  Segment position p holds
+// column xs - 4 + p.
+template <int Q, int NT, int V, bool EDGE, class Rel>
+__device__ __forceinline__ void ring_tile_vec(const VDom &d, const float *__restrict__ sb,
+                                              const float *const ey_slot[3], const Nb3 &Y,
+                                              const Nb3 &Z, float *__restrict__ fout, long long ro,
+                                              int xs, int tid, Rel &&release) {
+    using L = Lat<Q>;
+    static_assert(V == 2 || V == 4, "2 or 4 cells per thread");
+    constexpr int SEG = NT * V + 8;
+    constexpr int NZ = (Q == 9) ? 1 : 3;      // z-rows per ring slot
+    const int x0l = V * tid;
     auto ywall = [&](int k) { return EDGE && Y.wall[k]; };
-    auto v4 = [&](const float *row, int p, float out[4]) {
-        const float4 t = *reinterpret_cast<const float4 *>(row + p);
-        out[0] = t.x; out[1] = t.y; out[2] = t.z; out[3] = t.w;
+    auto zwall = [&](int k) { return EDGE && Z.wall[k]; };
+    auto vload = [&](const float *row, int p, float out[V]) {
+        if constexpr (V == 4) {
+            const float4 t = *reinterpret_cast<const float4 *>(row + p);
+            out[0] = t.x; out[1] = t.y; out[2] = t.z; out[3] = t.w;
+        } else {
+            const float2 t = *reinterpret_cast<const float2 *>(row + p);
+            out[0] = t.x; out[1] = t.y;
+        }
     };
-    float h[9][4];
+    float h[Q][V];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
+    for (int i = 0; i < Q; ++i) {
         const float *row = sb + i * SEG;
-        const bool bb = ywall(1 - L::ey(i));
+        const bool bb = ywall(1 - L::ey(i)) || zwall(1 - L::ez(i));
         const int s = bb ? 0 : -L::ex(i);
-        float B[4];
-        v4(row, x0l + 4, B);
+        float B[V];
+        vload(row, x0l + 4, B);
         if (s == 0) {
 #pragma unroll
-            for (int c = 0; c < 4; ++c) h[i][c] = B[c];
+            for (int c = 0; c < V; ++c) h[i][c] = B[c];
         } else if (s < 0) {
-            float A[4];
-            v4(row, x0l, A);
-            h[i][0] = A[3]; h[i][1] = B[0]; h[i][2] = B[1]; h[i][3] = B[2];
+            float A[V];
+            vload(row, x0l + 4 - V, A);
+            h[i][0] = A[V - 1];
+#pragma unroll
+            for (int c = 1; c < V; ++c) h[i][c] = B[c - 1];
         } else {
-            float C[4];
-            v4(row, x0l + 8, C);
-            h[i][0] = B[1]; h[i][1] = B[2]; h[i][2] = B[3]; h[i][3] = C[0];
+            float C[V];
+            vload(row, x0l + 4 + V, C);
+#pragma unroll
+            for (int c = 0; c < V - 1; ++c) h[i][c] = B[c + 1];
+            h[i][V - 1] = C[0];
         }
     }
-    // eps rows y-1, y, y+1 at columns x0-1 .. x0+4
-    float E[3][6];
+    // eps rows (y + dy, z + dz) at columns x0l-1 .. x0l+V; a D3Q19 corner row
+    // (dy, dz both nonzero) is only read at dx = 0
+    float E[3][NZ][V + 2];
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-        float A[4], B[4], C[4];
-        v4(ey_slot[r], x0l, A);
-        v4(ey_slot[r], x0l + 4, B);
-        v4(ey_slot[r], x0l + 8, C);
-        E[r][0] = A[3];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) E[r][c + 1] = B[c];
-        E[r][5] = C[0];
+        for (int q = 0; q < NZ; ++q) {
+            const float *row = ey_slot[r] + q * SEG;
+            float B[V];
+            vload(row, x0l + 4, B);
+#pragma unroll
+            for (int c = 0; c < V; ++c) E[r][q][c + 1] = B[c];
+            const bool side = (Q == 9) || r == 1 || q == 1;
+            if (side) {
+                float A[V], C[V];
+                vload(row, x0l + 4 - V, A);
+                vload(row, x0l + 4 + V, C);
+                E[r][q][0] = A[V - 1];
+                E[r][q][V + 1] = C[0];
+            } else {
+                E[r][q][0] = E[r][q][V + 1] = 0.f;    // never read
+            }
+        }
     }
     release();                  // the stage is no longer read
-    float out[9][4];
+    constexpr int ZC = (Q == 9) ? 0 : 1;    // the z-row of dz = 0
+    float out[Q][V];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        float hh[9], et[9], o[9];
-        const float e0 = E[1][c + 1];
+    for (int c = 0; c < V; ++c) {
+        float hh[Q], et[Q], o[Q];
+        const float e0 = E[1][ZC][c + 1];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
+        for (int i = 0; i < Q; ++i) {
             hh[i] = h[i][c];
-            const bool wall = ywall(1 + L::ey(i));
-            et[i] = (i == 0 || wall) ? e0 : E[1 + L::ey(i)][c + 1 + L::ex(i)];
+            const bool wall = ywall(1 + L::ey(i)) || zwall(1 + L::ez(i));
+            et[i] = (i == 0 || wall) ? e0 : E[1 + L::ey(i)][ZC + L::ez(i)][c + 1 + L::ex(i)];
         }
-        if (EDGE) apply_moving_wall<9>(d, Y.wall[2], Z, e0, hh);
-        collide<9>(d, hh, e0, et, o);
+        if (EDGE) apply_moving_wall<Q>(d, Y.wall[2], Z, e0, hh);
+        collide<Q>(d, hh, e0, et, o);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) out[i][c] = o[i];
+        for (int i = 0; i < Q; ++i) out[i][c] = o[i];
     }
     const int x0 = xs + x0l;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) st_masked<4>(fout + i * d.plane + ro, x0, d.nx, out[i]);
+    for (int i = 0; i < Q; ++i) st_masked<V>(fout + i * d.plane + ro, x0, d.nx, out[i]);
     if (x0 == 0) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i)
+        for (int i = 0; i < Q; ++i)
             if (L::ex(i) < 0) fout[i * d.plane + ro + d.nx] = out[i][0];
     }
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < V; ++c) {
         if (x0 + c == d.nx - 1) {
 #pragma unroll
-            for (int i = 0; i < 9; ++i)
+            for (int i = 0; i < Q; ++i)
                 if (L::ex(i) > 0) fout[i * d.plane + ro - 1] = out[i][c];
         }
     }
@@ -332,7 +356,7 @@ __device__ __forceinline__ void ring_tile(const VDom &d, const float *__restrict
     using L = Lat<Q>;
     constexpr int SEG = NT * CPT + 8;
     if constexpr (VEC) {
-        ring_tile_vec9<NT, EDGE>(d, sb, ey_slot, Y, Z, fout, ro, xs, tid, release);
+        ring_tile_vec<Q, NT, CPT, EDGE>(d, sb, ey_slot, Y, Z, fout, ro, xs, tid, release);
     } else {
         auto ywall = [&](int k) { return EDGE && Y.wall[k]; };
         auto zwall = [&](int k) { return EDGE && Z.wall[k]; };
@@ -717,9 +741,19 @@ cudaError_t launch_ring_batched(const VDom *doms, const Tile *strips, int nstrip
 cudaError_t launch_step_tma(int q, const VDom &d, const float *fin, float *fout, Launch L,
                             cudaStream_t stream) {
     const int nt = 32 * L.warps;
-    if (L.kind == 3 || L.kind == 5) {   // ring pipeline, 4 consecutive cells per thread (D2Q9)
-        if (q != 9 || L.cpt != 4) return cudaErrorInvalidValue;
+    if (L.kind == 3 || L.kind == 5) {   // ring pipeline, consecutive cells per thread
         const bool ws = L.kind == 5;
+        if (q == 19) {                  // 2 cells per thread
+            if (L.cpt != 2) return cudaErrorInvalidValue;
+            if (nt == 64)
+                return ws ? launch_ring_t<19, 64, 2, true, true>(d, fin, fout, L.rows, stream)
+                          : launch_ring_t<19, 64, 2, true>(d, fin, fout, L.rows, stream);
+            if (nt == 128)
+                return ws ? launch_ring_t<19, 128, 2, true, true>(d, fin, fout, L.rows, stream)
+                          : launch_ring_t<19, 128, 2, true>(d, fin, fout, L.rows, stream);
+            return cudaErrorInvalidValue;
+        }
+        if (q != 9 || L.cpt != 4) return cudaErrorInvalidValue;
         if (nt == 64)
             return ws ? launch_ring_t<9, 64, 4, true, true>(d, fin, fout, L.rows, stream)
                       : launch_ring_t<9, 64, 4, true>(d, fin, fout, L.rows, stream);

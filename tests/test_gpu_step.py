@@ -39,11 +39,14 @@ STEP_CASES = [
                           Launch(2, 8, 3, 4), Launch(4, 4, 6, 5)]),
     (19, (7, 9, 21), 6, [Launch(1, 2, 1), Launch(2, 2, 2), Launch(4, 1, 2), Launch(1, 4, 3, 1),
                          Launch(2, 4, 2, 1), Launch(1, 4, 3, 2), Launch(2, 4, 2, 2),
-                         Launch(1, 4, 3, 4), Launch(2, 4, 2, 4)]),
-    (19, (5, 4, 33), 2, [Launch(2, 2, 1), Launch(1, 8, 3, 1), Launch(1, 8, 2, 2)]),
+                         Launch(1, 4, 3, 4), Launch(2, 4, 2, 4), Launch(2, 4, 3, 3),
+                         Launch(2, 4, 2, 5), Launch(2, 2, 4, 5)]),
+    (19, (5, 4, 33), 2, [Launch(2, 2, 1), Launch(1, 8, 3, 1), Launch(1, 8, 2, 2), Launch(2, 2, 3, 3),
+                         Launch(2, 4, 4, 5)]),
     (19, (3, 3, 4), 0, [Launch(1, 2, 1), Launch(1, 4, 4, 1), Launch(1, 4, 4, 2)]),
-    (19, (1, 1, 2), 6, [Launch(1, 2, 1), Launch(1, 4, 3, 1), Launch(1, 4, 3, 2)]),
-    (19, (6, 30, 300), 4, [Launch(2, 4, 3, 2), Launch(1, 8, 3, 2), Launch(1, 8, 3, 4)]),
+    (19, (1, 1, 2), 6, [Launch(1, 2, 1), Launch(1, 4, 3, 1), Launch(1, 4, 3, 2), Launch(2, 4, 2, 5)]),
+    (19, (6, 30, 300), 4, [Launch(2, 4, 3, 2), Launch(1, 8, 3, 2), Launch(1, 8, 3, 4),
+                           Launch(2, 4, 3, 5), Launch(2, 2, 2, 3)]),
 ]
 
 
@@ -242,8 +245,9 @@ MOVING = [
       Launch(2, 4, 3, 4), Launch(4, 4, 3, 5)]),
     (9, (1, 1, 5), 2, (0.02, 0.0, 0.0), [Launch(2, 2, 1), Launch(2, 4, 2, 2)]),
     (19, (7, 9, 21), 6, (0.01, 0.003, -0.002),
-     [Launch(1, 2, 1), Launch(2, 2, 2), Launch(1, 4, 3, 1), Launch(2, 4, 2, 2)]),
-    (19, (4, 5, 9), 2, (0.0, 0.0, 0.01), [Launch(2, 2, 1), Launch(1, 8, 2, 2), Launch(1, 8, 2, 4)]),
+     [Launch(1, 2, 1), Launch(2, 2, 2), Launch(1, 4, 3, 1), Launch(2, 4, 2, 2), Launch(2, 4, 3, 5)]),
+    (19, (4, 5, 9), 2, (0.0, 0.0, 0.01), [Launch(2, 2, 1), Launch(1, 8, 2, 2), Launch(1, 8, 2, 4),
+                                          Launch(2, 4, 2, 5)]),
 ]
 
 
