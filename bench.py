@@ -49,9 +49,8 @@ TRAFFIC = {
     (4, 4, 4, 5, "05387f1b88f16d08"): (681875712 + 559799040 + 681548544 + 556076800) // 2,
 }
 _PIPELINE_SOURCES = ("vans_step_tma.cu", "vans_device.cuh", "vans_tma.cuh")
-KERNEL_SOURCES = {0: ("vans_step.cu", "vans_device.cuh"), 1: _PIPELINE_SOURCES,
-                  2: _PIPELINE_SOURCES, 3: _PIPELINE_SOURCES, 4: _PIPELINE_SOURCES,
-                  5: _PIPELINE_SOURCES}
+KERNEL_SOURCES = {0: ("vans_step.cu", "vans_device.cuh")}
+KERNEL_SOURCES.update({k: _PIPELINE_SOURCES for k in range(1, 8)})
 
 
 def kernel_hash(kind: int = 2) -> str:
@@ -67,7 +66,9 @@ KERNEL_NAMES = {0: "k_step<9,cpt>", 1: "k_step_tma<9,32*warps,cpt>",
                 2: "k_step_tma_ring<9,32*warps,cpt>",
                 3: "k_step_tma_ring<9,32*warps,4,contiguous>",
                 4: "k_step_tma_ring<9,32*warps,cpt,warp-specialised>",
-                5: "k_step_tma_ring<9,32*warps,4,contiguous,warp-specialised>"}
+                5: "k_step_tma_ring<9,32*warps,4,contiguous,warp-specialised>",
+                6: "k_step_tma_ilv<9,32*warps,cpt,strided>",
+                7: "k_step_tma_ilv<9,32*warps,4,contiguous>"}
 
 
 def peaks():

@@ -93,8 +93,13 @@ typedef struct {
  * kind 4, 5: kinds 2 and 3 with one extra producer warp per CTA (warps counts
  *         the compute warps only): stages are released per warp through
  *         "empty" mbarriers instead of a block-wide barrier per tile.
- *         The batched path takes kinds 0 and 2 (kind 2: one CTA per strip of
- *         up to 32 rows of one domain). */
+ * kind 6, 7: persistent CTAs that take tiles b, b+G, b+2G, ... of the row-major
+ *         tile order (the whole grid sweeps one band of rows), porosity rows
+ *         staged per tile, producer warp as in kinds 4, 5; 6 strided cells
+ *         (D2Q9 cpt 2, D3Q19 cpt 1; warps 4 or 8), 7 consecutive cells as in
+ *         kind 3.  Single-domain solver only.
+ *         The batched path takes kinds 0, 2, 4 and 5 (one CTA per strip of
+ *         up to 32 rows of one domain; kind 5 D2Q9 only). */
 typedef struct {
     int cpt;
     int warps;

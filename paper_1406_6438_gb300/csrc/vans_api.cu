@@ -110,12 +110,16 @@ bool launch_ok(const vans_launch *c, int q, bool batched) {
         if (c->warps < 1 || c->warps > 8 || c->rows < 1 || c->rows > 8) return false;
         return c->warps * c->rows <= 8;
     }
-    if (c->kind < 1 || c->kind > 5 || (batched && c->kind != 2 && c->kind < 4)) return false;
+    if (c->kind < 1 || c->kind > 7 || (batched && c->kind != 2 && c->kind != 4 && c->kind != 5))
+        return false;
     if (c->rows < 2 || c->rows > 6) return false;
     // the instantiated pipeline shapes
     const int nt = 32 * c->warps;
-    if (c->kind == 3 || c->kind == 5)
+    if (c->kind == 3 || c->kind == 5 || c->kind == 7)
         return (nt == 64 || nt == 128) && c->cpt == (q == 9 ? 4 : 2) && (q == 9 || !batched);
+    if (c->kind == 6)
+        return q == 9 ? (c->cpt == 2 && (nt == 128 || nt == 256))
+                      : (c->cpt == 1 && (nt == 128 || nt == 256));
     if (q == 9)
         return (nt == 128 && (c->cpt == 2 || c->cpt == 4)) || (nt == 256 && c->cpt <= 2);
     return (nt == 128 && c->cpt <= 2) || (nt == 256 && c->cpt == 1);
@@ -358,15 +362,17 @@ std::vector<Launch> candidates(int q, bool batched) {
                             {1, 8, 4, 2}, {2, 8, 3, 2}, {4, 4, 2, 3}, {4, 4, 3, 3},
                             {4, 2, 3, 3}, {4, 2, 4, 3}, {2, 8, 2, 4}, {4, 4, 2, 4},
                             {4, 2, 2, 5}, {4, 4, 2, 5}, {4, 4, 4, 5}, {4, 4, 5, 5},
-                            {4, 4, 6, 5}};
-        c.insert(c.end(), t, t + 25);
+                            {4, 4, 6, 5}, {2, 8, 2, 6}, {2, 4, 2, 6}, {4, 4, 4, 7},
+                            {4, 2, 4, 7}, {4, 4, 2, 7}};
+        c.insert(c.end(), t, t + 30);
     } else {
         const Launch t[] = {{1, 4, 3, 1}, {1, 4, 4, 1}, {2, 4, 2, 1}, {2, 4, 3, 1},
                             {1, 8, 2, 1}, {1, 8, 3, 1}, {1, 4, 3, 2}, {2, 4, 2, 2},
                             {2, 4, 3, 2}, {1, 8, 2, 2}, {1, 8, 3, 2}, {1, 4, 3, 4},
                             {1, 8, 2, 4}, {2, 4, 2, 3}, {2, 4, 3, 3}, {2, 2, 3, 3},
-                            {2, 4, 2, 5}, {2, 4, 3, 5}, {2, 4, 4, 5}, {2, 2, 3, 5}};
-        c.insert(c.end(), t, t + 20);
+                            {2, 4, 2, 5}, {2, 4, 3, 5}, {2, 4, 4, 5}, {2, 2, 3, 5},
+                            {1, 4, 3, 6}, {1, 8, 3, 6}, {2, 4, 3, 7}, {2, 2, 3, 7}};
+        c.insert(c.end(), t, t + 24);
     }
     return c;
 }

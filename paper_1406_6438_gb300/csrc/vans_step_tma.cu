@@ -21,9 +21,12 @@ template <int Q> struct EpsRows;
 template <> struct EpsRows<9> { static constexpr int N = 3; };    // dy = -1, 0, 1
 template <> struct EpsRows<19> { static constexpr int N = 9; };   // (dy, dz) in {-1,0,1}^2
 
+// Stage slot of the porosity row (y + dy, z + dz): D2Q9 dy + 1; D3Q19 the
+// three z-rows of one dy side by side, (dy + 1) * 3 + dz + 1 (the layout of
+// the ring slots, so the same tile compute reads both)
 template <int Q>
 __host__ __device__ constexpr int eps_slot(int dy, int dz) {
-    return Q == 9 ? dy + 1 : (dz + 1) * 3 + (dy + 1);
+    return Q == 9 ? dy + 1 : (dy + 1) * 3 + (dz + 1);
 }
 
 template <int Q>
@@ -64,13 +67,16 @@ __device__ __forceinline__ void issue_tile(const VDom &d, const float *__restric
         const long long ro = bb ? row_offset(d, y, z) : row_offset(d, Y.r[1 - ey], Z.r[1 - ez]);
         bulk_g2s(sb + i * SEG, fin + si * d.plane + ro + xs - 4, bytes, bar);
     }
+    // the porosity rows are read again by the tiles of the neighbouring rows:
+    // keep them in L2 longest
+    const uint64_t again = l2_evict_last();
 #pragma unroll
     for (int dz = -1; dz <= 1; ++dz)
 #pragma unroll
         for (int dy = -1; dy <= 1; ++dy) {
             if (Q == 9 && dz != 0) continue;
             const float *src = d.eps + row_offset(d, Y.r[1 + dy], Z.r[1 + dz]) + xs - 4;
-            bulk_g2s(sb + (Q + eps_slot<Q>(dy, dz)) * SEG, src, bytes, bar);
+            bulk_g2s_hint(sb + (Q + eps_slot<Q>(dy, dz)) * SEG, src, bytes, bar, again);
         }
     (void)NS;
 }
@@ -596,6 +602,127 @@ __global__ void __launch_bounds__(WS ? NT + 32 : NT) k_step_tma_ring(const VDom 
         ring_strip<Q, NT, CPT, VEC>(d, fin, fout, xt * NT * CPT, z, y0, y1, stages, smem);
 }
 
+// Interleaved persistent step.  CTA b of G takes tiles b, b + G, b + 2G, ...
+// of the row-major tile order, so at any moment the whole grid works on one
+// band of neighbouring rows: the DRAM sees each population plane as one
+// advancing window instead of one stream per CTA, and the porosity rows a tile
+// shares with the tiles of the rows above and below (3 per tile in D2Q9, 9 in
+// D3Q19, copied with the population rows into the stage) come mostly from L2.
+// Warp-specialised like ring_strip_ws: NT compute threads + one producer warp,
+// full/empty barriers per stage, release as soon as a warp's lanes have read
+// the stage.  stages <= kBarBytes / 16.
+template <int Q, int NT, int CPT, bool VEC>
+__global__ void __launch_bounds__(NT + 32) k_step_tma_ilv(const VDom d, const float *__restrict__ fin,
+                                                           float *__restrict__ fout, int ntx,
+                                                           int ntiles, int stages) {
+    constexpr int TW = NT * CPT;
+    constexpr int SEG = TW + 8;
+    constexpr int NS = Q + EpsRows<Q>::N;
+    constexpr int NZR = (Q == 9) ? 1 : 3;
+    constexpr int NCW = NT / 32;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
+    uint64_t *empty = full + stages;
+    float *buf = reinterpret_cast<float *>(smem + kBarBytes);
+    const int tid = threadIdx.x;
+    const int G = (int)gridDim.x, b = (int)blockIdx.x;
+    const int n = (ntiles - b + G - 1) / G;        // tiles of this CTA
+    if (n <= 0) return;
+    // tile cursor (row, column block), advanced by G tiles at a time
+    const int drow = G / ntx, dxt = G - (G / ntx) * ntx;
+    auto advance = [&](int &row, int &xt) {
+        row += drow;
+        xt += dxt;
+        if (xt >= ntx) { xt -= ntx; ++row; }
+    };
+
+    if (tid == 0) {
+        for (int s = 0; s < stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], NCW);
+        }
+        mbar_init_fence();
+    }
+    __syncthreads();
+    if (tid >= NT) {                      // producer warp
+        if (tid != NT) return;
+        int row = b / ntx, xt = b - (b / ntx) * ntx;
+        int issued = 0;
+        bool ok = true;
+        for (int k = 0; k < n; ++k) {
+            const int s = k % stages;
+            if (k >= stages) {
+                ok = mbar_wait_bounded(&empty[s], (uint32_t)(((k / stages) - 1) & 1));
+                if (!ok) break;
+                fence_proxy_async_smem();
+            }
+            issue_tile<Q, TW>(d, fin, row, xt * TW, buf + s * (NS * SEG), &full[s]);
+            issued = k + 1;
+            advance(row, xt);
+        }
+        if (!ok) {
+            if (d.status) atomicOr(d.status, 2);
+            const int first = issued > stages ? issued - stages : 0;
+            for (int j = first; j < issued; ++j)
+                mbar_wait_bounded(&full[j % stages], (uint32_t)((j / stages) & 1));
+        }
+        return;
+    }
+    const int lane = tid & 31;
+    int row = b / ntx, xt = b - (b / ntx) * ntx;
+    int s = 0;
+    uint32_t par = 0;
+    for (int k = 0; k < n; ++k) {
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[s], par))) {
+            if (lane == 0 && d.status) atomicOr(d.status, 2);
+            return;
+        }
+        int y, z;
+        Nb3 Y, Z;
+        row_nbs<Q>(d, row, y, z, Y, Z);
+        const float *sb = buf + s * (NS * SEG);
+        const float *ey_slot[3] = {sb + Q * SEG, sb + (Q + NZR) * SEG, sb + (Q + 2 * NZR) * SEG};
+        const long long ro = row_offset(d, y, z);
+        uint64_t *const emp = &empty[s];
+        auto release = [&] {
+            __syncwarp();       // every lane's reads of the stage precede the arrive
+            if (lane == 0) mbar_arrive(emp);
+        };
+        const int xs = xt * TW;
+        if (Q == 19 || Y.wall[0] || Y.wall[2] || Z.wall[0] || Z.wall[2])
+            ring_tile<Q, NT, CPT, VEC, true>(d, sb, ey_slot, Y, Z, fout, ro, xs, tid, release);
+        else
+            ring_tile<Q, NT, CPT, VEC, false>(d, sb, ey_slot, Y, Z, fout, ro, xs, tid, release);
+        advance(row, xt);
+        if (++s == stages) { s = 0; par ^= 1u; }
+    }
+}
+
+template <int Q, int NT, int CPT, bool VEC>
+static cudaError_t launch_ilv_t(const VDom &d, const float *fin, float *fout, int stages,
+                                cudaStream_t stream) {
+    constexpr int TW = NT * CPT;
+    constexpr int NS = Q + EpsRows<Q>::N;
+    const size_t smem = kBarBytes + (size_t)stages * NS * (TW + 8) * sizeof(float);
+    if (stages < 2 || stages > kBarBytes / 16 || smem > 227 * 1024) return cudaErrorInvalidValue;
+    auto kern = k_step_tma_ilv<Q, NT, CPT, VEC>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT + 32, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    const int ntx = (d.nx + TW - 1) / TW;
+    const long long ntiles = (long long)ntx * d.rows;
+    if (ntiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    long long grid = (long long)sms * occ;
+    if (grid > ntiles) grid = ntiles;
+    kern<<<(unsigned)grid, NT + 32, smem, stream>>>(d, fin, fout, ntx, (int)ntiles, stages);
+    return cudaGetLastError();
+}
+
 // Batched D2Q9: CTA b takes strip b of a table built on the host (domain,
 // column block, rows y0..y1-1; largest strips first) and advances it with the
 // porosity-ring pipeline, using that domain's descriptor and buffers.
@@ -741,6 +868,20 @@ cudaError_t launch_ring_batched(const VDom *doms, const Tile *strips, int nstrip
 cudaError_t launch_step_tma(int q, const VDom &d, const float *fin, float *fout, Launch L,
                             cudaStream_t stream) {
     const int nt = 32 * L.warps;
+    if (L.kind == 6) {                  // interleaved tiles, strided cells per thread
+        if (q == 9 && nt == 128 && L.cpt == 2) return launch_ilv_t<9, 128, 2, false>(d, fin, fout, L.rows, stream);
+        if (q == 9 && nt == 256 && L.cpt == 2) return launch_ilv_t<9, 256, 2, false>(d, fin, fout, L.rows, stream);
+        if (q == 19 && nt == 128 && L.cpt == 1) return launch_ilv_t<19, 128, 1, false>(d, fin, fout, L.rows, stream);
+        if (q == 19 && nt == 256 && L.cpt == 1) return launch_ilv_t<19, 256, 1, false>(d, fin, fout, L.rows, stream);
+        return cudaErrorInvalidValue;
+    }
+    if (L.kind == 7) {                  // interleaved tiles, consecutive cells per thread
+        if (q == 9 && nt == 64 && L.cpt == 4) return launch_ilv_t<9, 64, 4, true>(d, fin, fout, L.rows, stream);
+        if (q == 9 && nt == 128 && L.cpt == 4) return launch_ilv_t<9, 128, 4, true>(d, fin, fout, L.rows, stream);
+        if (q == 19 && nt == 64 && L.cpt == 2) return launch_ilv_t<19, 64, 2, true>(d, fin, fout, L.rows, stream);
+        if (q == 19 && nt == 128 && L.cpt == 2) return launch_ilv_t<19, 128, 2, true>(d, fin, fout, L.rows, stream);
+        return cudaErrorInvalidValue;
+    }
     if (L.kind == 3 || L.kind == 5) {   // ring pipeline, consecutive cells per thread
         const bool ws = L.kind == 5;
         if (q == 19) {                  // 2 cells per thread

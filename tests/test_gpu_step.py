@@ -24,29 +24,34 @@ STEP_CASES = [
     (9, (1, 13, 37), 2, [Launch(1, 1, 2), Launch(2, 2, 1), Launch(4, 1, 2), Launch(4, 4, 1),
                          Launch(2, 4, 3, 1), Launch(1, 8, 2, 1), Launch(2, 4, 3, 2),
                          Launch(4, 4, 3, 3), Launch(4, 2, 2, 3), Launch(2, 4, 3, 4),
-                         Launch(4, 4, 3, 5), Launch(4, 2, 2, 5)]),
+                         Launch(4, 4, 3, 5), Launch(4, 2, 2, 5), Launch(2, 4, 2, 6),
+                         Launch(2, 8, 3, 6), Launch(4, 4, 2, 7), Launch(4, 2, 3, 7)]),
     (9, (1, 6, 5), 0, [Launch(4, 2, 1), Launch(1, 2, 1), Launch(4, 4, 2, 1), Launch(1, 8, 2, 2),
                        Launch(4, 2, 3, 3)]),
     (9, (1, 1, 1), 0, [Launch(4, 2, 1), Launch(2, 4, 3, 1), Launch(2, 4, 3, 2), Launch(4, 4, 3, 3),
-                       Launch(2, 4, 3, 4), Launch(4, 4, 3, 5)]),
+                       Launch(2, 4, 3, 4), Launch(4, 4, 3, 5), Launch(2, 4, 2, 6), Launch(4, 4, 2, 7)]),
     (9, (1, 1, 3), 2, [Launch(1, 2, 1), Launch(2, 8, 3, 1), Launch(2, 8, 2, 2), Launch(4, 2, 2, 3)]),
     (9, (1, 9, 300), 2, [Launch(2, 2, 2), Launch(4, 2, 1), Launch(2, 4, 4, 1), Launch(1, 8, 4, 1),
                          Launch(4, 4, 3, 2), Launch(1, 8, 4, 2), Launch(4, 4, 4, 3),
-                         Launch(4, 4, 3, 4), Launch(1, 8, 4, 4), Launch(4, 2, 4, 5)]),
+                         Launch(4, 4, 3, 4), Launch(1, 8, 4, 4), Launch(4, 2, 4, 5),
+                         Launch(2, 4, 3, 6), Launch(4, 4, 2, 7)]),
     (9, (1, 7, 1100), 0, [Launch(2, 4, 3, 1), Launch(4, 4, 3, 1), Launch(2, 4, 4, 2),
                           Launch(4, 2, 5, 3)]),
     (9, (1, 40, 700), 2, [Launch(2, 8, 3, 2), Launch(1, 8, 5, 2), Launch(4, 4, 3, 3),
-                          Launch(2, 8, 3, 4), Launch(4, 4, 6, 5)]),
+                          Launch(2, 8, 3, 4), Launch(4, 4, 6, 5), Launch(2, 8, 4, 6), Launch(4, 2, 5, 7)]),
     (19, (7, 9, 21), 6, [Launch(1, 2, 1), Launch(2, 2, 2), Launch(4, 1, 2), Launch(1, 4, 3, 1),
                          Launch(2, 4, 2, 1), Launch(1, 4, 3, 2), Launch(2, 4, 2, 2),
                          Launch(1, 4, 3, 4), Launch(2, 4, 2, 4), Launch(2, 4, 3, 3),
-                         Launch(2, 4, 2, 5), Launch(2, 2, 4, 5)]),
+                         Launch(2, 4, 2, 5), Launch(2, 2, 4, 5), Launch(1, 4, 2, 6),
+                         Launch(1, 8, 3, 6), Launch(2, 4, 2, 7), Launch(2, 2, 3, 7)]),
     (19, (5, 4, 33), 2, [Launch(2, 2, 1), Launch(1, 8, 3, 1), Launch(1, 8, 2, 2), Launch(2, 2, 3, 3),
                          Launch(2, 4, 4, 5)]),
     (19, (3, 3, 4), 0, [Launch(1, 2, 1), Launch(1, 4, 4, 1), Launch(1, 4, 4, 2)]),
-    (19, (1, 1, 2), 6, [Launch(1, 2, 1), Launch(1, 4, 3, 1), Launch(1, 4, 3, 2), Launch(2, 4, 2, 5)]),
+    (19, (1, 1, 2), 6, [Launch(1, 2, 1), Launch(1, 4, 3, 1), Launch(1, 4, 3, 2), Launch(2, 4, 2, 5),
+                        Launch(1, 4, 2, 6), Launch(2, 4, 2, 7)]),
     (19, (6, 30, 300), 4, [Launch(2, 4, 3, 2), Launch(1, 8, 3, 2), Launch(1, 8, 3, 4),
-                           Launch(2, 4, 3, 5), Launch(2, 2, 2, 3)]),
+                           Launch(2, 4, 3, 5), Launch(2, 2, 2, 3), Launch(1, 8, 2, 6),
+                           Launch(2, 4, 3, 7)]),
 ]
 
 
@@ -108,7 +113,8 @@ def test_d3q19_duct_downsized():
 
 
 @pytest.mark.parametrize("L", [Launch(4, 4, 1), Launch(2, 4, 3, 1), Launch(2, 8, 3, 2),
-                               Launch(4, 4, 3, 3), Launch(4, 4, 3, 4), Launch(4, 4, 3, 5)])
+                               Launch(4, 4, 3, 3), Launch(4, 4, 3, 4), Launch(4, 4, 3, 5),
+                               Launch(2, 4, 2, 6), Launch(4, 4, 2, 7)])
 def test_graph_replay_equals_single_launches(L):
     """vans_step(n) replays a captured CUDA graph for long runs; the result is
     bit-identical to n single steps."""
@@ -153,7 +159,7 @@ def test_autotune_leaves_state_unchanged():
     a.step(10)
     b.step(10)
     L = a.autotune()
-    assert L.cpt in (1, 2, 4) and L.kind in (0, 1, 2, 3, 4, 5)
+    assert L.cpt in (1, 2, 4) and L.kind in (0, 1, 2, 3, 4, 5, 6, 7)
     b.launch = L
     a.step(10)
     b.step(10)
@@ -177,7 +183,8 @@ def test_launch_shapes_agree_on_a_long_run():
     ref = None
     for L in (Launch(1, 2, 1), Launch(2, 4, 2), Launch(4, 4, 1), Launch(4, 2, 4),
               Launch(2, 4, 3, 1), Launch(1, 8, 4, 1), Launch(4, 4, 2, 1), Launch(2, 8, 3, 2),
-              Launch(4, 4, 3, 3), Launch(2, 8, 3, 4), Launch(4, 4, 2, 5)):
+              Launch(4, 4, 3, 3), Launch(2, 8, 3, 4), Launch(4, 4, 2, 5), Launch(2, 8, 2, 6),
+              Launch(4, 4, 2, 7)):
         rho, u, f = gpu_run(p, eps, n, launch=L)
         if ref is None:
             ref = u
@@ -243,9 +250,11 @@ MOVING = [
     (9, (1, 13, 37), 2, (0.01, 0.002, 0.0),
      [Launch(4, 4, 1), Launch(1, 2, 1), Launch(2, 4, 3, 1), Launch(2, 4, 3, 2), Launch(4, 4, 3, 3),
       Launch(2, 4, 3, 4), Launch(4, 4, 3, 5)]),
-    (9, (1, 1, 5), 2, (0.02, 0.0, 0.0), [Launch(2, 2, 1), Launch(2, 4, 2, 2)]),
+    (9, (1, 1, 5), 2, (0.02, 0.0, 0.0), [Launch(2, 2, 1), Launch(2, 4, 2, 2), Launch(2, 4, 2, 6),
+                                         Launch(4, 4, 3, 7)]),
     (19, (7, 9, 21), 6, (0.01, 0.003, -0.002),
-     [Launch(1, 2, 1), Launch(2, 2, 2), Launch(1, 4, 3, 1), Launch(2, 4, 2, 2), Launch(2, 4, 3, 5)]),
+     [Launch(1, 2, 1), Launch(2, 2, 2), Launch(1, 4, 3, 1), Launch(2, 4, 2, 2), Launch(2, 4, 3, 5),
+      Launch(1, 4, 2, 6), Launch(2, 4, 2, 7)]),
     (19, (4, 5, 9), 2, (0.0, 0.0, 0.01), [Launch(2, 2, 1), Launch(1, 8, 2, 2), Launch(1, 8, 2, 4),
                                           Launch(2, 4, 2, 5)]),
 ]
