@@ -110,8 +110,7 @@ bool launch_ok(const vans_launch *c, int q, bool batched) {
         if (c->warps < 1 || c->warps > 8 || c->rows < 1 || c->rows > 8) return false;
         return c->warps * c->rows <= 8;
     }
-    if (c->kind < 1 || c->kind > 7 || (batched && c->kind != 2 && c->kind != 4 && c->kind != 5))
-        return false;
+    if (c->kind < 1 || c->kind > 7 || (batched && (c->kind == 1 || c->kind == 3))) return false;
     if (c->rows < 2 || c->rows > 6) return false;
     // the instantiated pipeline shapes
     const int nt = 32 * c->warps;
@@ -119,7 +118,7 @@ bool launch_ok(const vans_launch *c, int q, bool batched) {
         return (nt == 64 || nt == 128) && c->cpt == (q == 9 ? 4 : 2) && (q == 9 || !batched);
     if (c->kind == 6)
         return q == 9 ? (c->cpt == 2 && (nt == 128 || nt == 256))
-                      : (c->cpt == 1 && (nt == 128 || nt == 256));
+                      : (c->cpt == 1 && (nt == 128 || nt == 256) && !batched);
     if (q == 9)
         return (nt == 128 && (c->cpt == 2 || c->cpt == 4)) || (nt == 256 && c->cpt <= 2);
     return (nt == 128 && c->cpt <= 2) || (nt == 256 && c->cpt == 1);
@@ -184,7 +183,8 @@ void drop_graph(vans_t h) {
 // one batched step with the handle's launch (strip kernels for kinds 2, 4, 5)
 cudaError_t batched_step(vans_t h, cudaStream_t s, int par) {
     if (h->L.kind != 0)
-        return vans::launch_ring_batched(h->doms_d, h->tiles_d, (int)h->tiles.size(), par, h->L, s);
+        return vans::launch_ring_batched(h->doms_d, h->tiles_d, (int)h->tiles.size(), par, h->L,
+                                         h->flag + 1, s);
     return vans::launch_step_batched(h->doms_d, h->tiles_d, (int)h->tiles.size(), par, h->L,
                                      h->grid, s);
 }
@@ -270,6 +270,16 @@ constexpr int kStripRows = 32;   // rows per strip of the batched pipeline kerne
 void build_tiles(vans_t h, const Launch &L, std::vector<Tile> &out) {
     out.clear();
     const int bx = 32 * L.cpt * L.warps;
+    if (L.kind == 6 || L.kind == 7) {
+        // every row of every domain in column blocks, domain after domain: the
+        // persistent CTAs take tiles b, b + G, ... of this order
+        for (int d = 0; d < h->n; ++d) {
+            const VDom &D = h->doms[d];
+            for (int r = 0; r < D.rows; ++r)
+                for (int x = 0; x < D.nx; x += bx) out.push_back(Tile{d, r, x, 0});
+        }
+        return;
+    }
     if (L.kind != 0) {
         // strips of up to kStripRows rows per column block, largest first so the
         // last wave of CTAs holds the short ones
@@ -350,8 +360,9 @@ std::vector<Launch> candidates(int q, bool batched) {
     if (batched) {
         const Launch t[] = {{2, 4, 3, 2}, {4, 4, 2, 2}, {4, 4, 3, 2}, {2, 8, 2, 2}, {2, 8, 3, 2},
                             {1, 8, 3, 2}, {2, 8, 2, 4}, {2, 4, 2, 4}, {4, 2, 2, 5}, {4, 2, 3, 5},
-                            {4, 4, 2, 5}, {4, 4, 3, 5}, {4, 4, 4, 5}};
-        c.insert(c.end(), t, t + 13);
+                            {4, 4, 2, 5}, {4, 4, 3, 5}, {4, 4, 4, 5}, {2, 4, 2, 6}, {2, 8, 2, 6},
+                            {4, 2, 4, 7}, {4, 2, 3, 7}, {4, 4, 2, 7}, {4, 4, 4, 7}};
+        c.insert(c.end(), t, t + 19);
         return c;
     }
     // bulk-copy pipeline shapes {cpt, warps, stages, kind}

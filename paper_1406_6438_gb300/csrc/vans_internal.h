@@ -58,8 +58,9 @@ cudaError_t launch_step_monitor(int q, const VDom &d, const float *fin, float *f
                                 float *u, float *stats, cudaStream_t stream);
 cudaError_t launch_step_tma(int q, const VDom &d, const float *fin, float *fout, Launch L,
                             cudaStream_t stream);
+// kinds 2, 4, 5: strip table (one CTA per strip); 6, 7: interleaved tile table
 cudaError_t launch_ring_batched(const VDom *doms, const Tile *strips, int nstrips, int parity,
-                                Launch L, cudaStream_t stream);
+                                Launch L, int *status, cudaStream_t stream);
 cudaError_t launch_step_batched(const VDom *doms_dev, const Tile *tiles_dev, int ntiles, int parity,
                                 Launch L, int grid, cudaStream_t stream);
 int batched_blocks_per_sm(Launch L);

@@ -603,24 +603,71 @@ __global__ void __launch_bounds__(WS ? NT + 32 : NT) k_step_tma_ring(const VDom 
 }
 
 // Interleaved persistent step.  CTA b of G takes tiles b, b + G, b + 2G, ...
-// of the row-major tile order, so at any moment the whole grid works on one
-// band of neighbouring rows: the DRAM sees each population plane as one
-// advancing window instead of one stream per CTA, and the porosity rows a tile
-// shares with the tiles of the rows above and below (3 per tile in D2Q9, 9 in
-// D3Q19, copied with the population rows into the stage) come mostly from L2.
-// Warp-specialised like ring_strip_ws: NT compute threads + one producer warp,
-// full/empty barriers per stage, release as soon as a warp's lanes have read
-// the stage.  stages <= kBarBytes / 16.
-template <int Q, int NT, int CPT, bool VEC>
-__global__ void __launch_bounds__(NT + 32) k_step_tma_ilv(const VDom d, const float *__restrict__ fin,
-                                                           float *__restrict__ fout, int ntx,
-                                                           int ntiles, int stages) {
+// of a tile order (row-major for one domain; domain after domain for a batch),
+// so at any moment the whole grid works on one band of neighbouring rows: the
+// DRAM sees each population plane as one advancing window instead of one
+// stream per CTA, no CTA restarts its pipeline between runs of rows, and the
+// porosity rows a tile shares with the tiles of the rows above and below (3
+// per tile in D2Q9, 9 in D3Q19, copied with the population rows into the
+// stage) come mostly from L2.  Warp-specialised like ring_strip_ws: NT compute
+// threads + one producer warp, full/empty barriers per stage, release as soon
+// as a warp's lanes have read the stage.  stages <= kBarBytes / 16.
+//
+// A cursor walks this CTA's tiles: load() fetches the current tile's
+// description (for a batch, its table entry and its domain's descriptor, into
+// registers), dom(), fin(), fout(), row(), xs() describe it and next() moves G
+// tiles on.
+struct IlvCursor {             // one domain: (row, column block), no table
+    const VDom *d;
+    const float *f_in;
+    float *f_out;
+    int row_, xt, ntx, drow, dxt;
+    __device__ IlvCursor(const VDom &dd, const float *fi, float *fo, int b, int G, int ntx_)
+        : d(&dd), f_in(fi), f_out(fo), row_(b / ntx_), xt(b - (b / ntx_) * ntx_), ntx(ntx_),
+          drow(G / ntx_), dxt(G - (G / ntx_) * ntx_) {}
+    __device__ void load(int) {}
+    __device__ const VDom &dom() const { return *d; }
+    __device__ const float *fin() const { return f_in; }
+    __device__ float *fout() const { return f_out; }
+    __device__ int row() const { return row_; }
+    __device__ int xs(int TW) const { return xt * TW; }
+    __device__ void next() {
+        row_ += drow;
+        xt += dxt;
+        if (xt >= ntx) { xt -= ntx; ++row_; }
+    }
+};
+
+struct IlvBatchCursor {        // a batch: tile table {dom, row, x0}, descriptor per domain
+    const VDom *doms;
+    const Tile *tiles;
+    int t, G, parity;
+    Tile T;
+    VDom D;                    // register copy of the current tile's descriptor
+    __device__ IlvBatchCursor(const VDom *ds, const Tile *ts, int b, int G_, int par)
+        : doms(ds), tiles(ts), t(b), G(G_), parity(par) {}
+    __device__ void load(int ntiles) {
+        if (t < ntiles) {
+            T = tiles[t];
+            D = doms[T.dom];
+        }
+    }
+    __device__ const VDom &dom() const { return D; }
+    __device__ const float *fin() const { return parity ? D.f[1] : D.f[0]; }
+    __device__ float *fout() const { return parity ? D.f[0] : D.f[1]; }
+    __device__ int row() const { return T.row; }
+    __device__ int xs(int) const { return T.x0; }
+    __device__ void next() { t += G; }
+};
+
+template <int Q, int NT, int CPT, bool VEC, class Cur>
+__device__ __forceinline__ void ilv_run(Cur cur, const int *status, int ntiles, int stages,
+                                        unsigned char *smem) {
     constexpr int TW = NT * CPT;
     constexpr int SEG = TW + 8;
     constexpr int NS = Q + EpsRows<Q>::N;
     constexpr int NZR = (Q == 9) ? 1 : 3;
     constexpr int NCW = NT / 32;
-    extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
     uint64_t *empty = full + stages;
     float *buf = reinterpret_cast<float *>(smem + kBarBytes);
@@ -628,13 +675,7 @@ __global__ void __launch_bounds__(NT + 32) k_step_tma_ilv(const VDom d, const fl
     const int G = (int)gridDim.x, b = (int)blockIdx.x;
     const int n = (ntiles - b + G - 1) / G;        // tiles of this CTA
     if (n <= 0) return;
-    // tile cursor (row, column block), advanced by G tiles at a time
-    const int drow = G / ntx, dxt = G - (G / ntx) * ntx;
-    auto advance = [&](int &row, int &xt) {
-        row += drow;
-        xt += dxt;
-        if (xt >= ntx) { xt -= ntx; ++row; }
-    };
+    int *const st = const_cast<int *>(status);
 
     if (tid == 0) {
         for (int s = 0; s < stages; ++s) {
@@ -646,7 +687,6 @@ __global__ void __launch_bounds__(NT + 32) k_step_tma_ilv(const VDom d, const fl
     __syncthreads();
     if (tid >= NT) {                      // producer warp
         if (tid != NT) return;
-        int row = b / ntx, xt = b - (b / ntx) * ntx;
         int issued = 0;
         bool ok = true;
         for (int k = 0; k < n; ++k) {
@@ -656,12 +696,14 @@ __global__ void __launch_bounds__(NT + 32) k_step_tma_ilv(const VDom d, const fl
                 if (!ok) break;
                 fence_proxy_async_smem();
             }
-            issue_tile<Q, TW>(d, fin, row, xt * TW, buf + s * (NS * SEG), &full[s]);
+            cur.load(ntiles);
+            issue_tile<Q, TW>(cur.dom(), cur.fin(), cur.row(), cur.xs(TW), buf + s * (NS * SEG),
+                              &full[s]);
             issued = k + 1;
-            advance(row, xt);
+            cur.next();
         }
         if (!ok) {
-            if (d.status) atomicOr(d.status, 2);
+            if (st) atomicOr(st, 2);
             const int first = issued > stages ? issued - stages : 0;
             for (int j = first; j < issued; ++j)
                 mbar_wait_bounded(&full[j % stages], (uint32_t)((j / stages) & 1));
@@ -669,17 +711,18 @@ __global__ void __launch_bounds__(NT + 32) k_step_tma_ilv(const VDom d, const fl
         return;
     }
     const int lane = tid & 31;
-    int row = b / ntx, xt = b - (b / ntx) * ntx;
     int s = 0;
     uint32_t par = 0;
     for (int k = 0; k < n; ++k) {
         if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[s], par))) {
-            if (lane == 0 && d.status) atomicOr(d.status, 2);
+            if (lane == 0 && st) atomicOr(st, 2);
             return;
         }
+        cur.load(ntiles);
+        const VDom &d = cur.dom();
         int y, z;
         Nb3 Y, Z;
-        row_nbs<Q>(d, row, y, z, Y, Z);
+        row_nbs<Q>(d, cur.row(), y, z, Y, Z);
         const float *sb = buf + s * (NS * SEG);
         const float *ey_slot[3] = {sb + Q * SEG, sb + (Q + NZR) * SEG, sb + (Q + 2 * NZR) * SEG};
         const long long ro = row_offset(d, y, z);
@@ -688,14 +731,35 @@ __global__ void __launch_bounds__(NT + 32) k_step_tma_ilv(const VDom d, const fl
             __syncwarp();       // every lane's reads of the stage precede the arrive
             if (lane == 0) mbar_arrive(emp);
         };
-        const int xs = xt * TW;
+        const int xs = cur.xs(TW);
         if (Q == 19 || Y.wall[0] || Y.wall[2] || Z.wall[0] || Z.wall[2])
-            ring_tile<Q, NT, CPT, VEC, true>(d, sb, ey_slot, Y, Z, fout, ro, xs, tid, release);
+            ring_tile<Q, NT, CPT, VEC, true>(d, sb, ey_slot, Y, Z, cur.fout(), ro, xs, tid, release);
         else
-            ring_tile<Q, NT, CPT, VEC, false>(d, sb, ey_slot, Y, Z, fout, ro, xs, tid, release);
-        advance(row, xt);
+            ring_tile<Q, NT, CPT, VEC, false>(d, sb, ey_slot, Y, Z, cur.fout(), ro, xs, tid, release);
+        cur.next();
         if (++s == stages) { s = 0; par ^= 1u; }
     }
+}
+
+template <int Q, int NT, int CPT, bool VEC>
+__global__ void __launch_bounds__(NT + 32) k_step_tma_ilv(const VDom d, const float *__restrict__ fin,
+                                                           float *__restrict__ fout, int ntx,
+                                                           int ntiles, int stages) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    ilv_run<Q, NT, CPT, VEC>(IlvCursor(d, fin, fout, (int)blockIdx.x, (int)gridDim.x, ntx), d.status,
+                             ntiles, stages, smem);
+}
+
+// Batched D2Q9, interleaved: the tile table lists every (domain, row, column
+// block) of the batch, domain after domain, row-major within a domain.
+template <int NT, int CPT, bool VEC>
+__global__ void __launch_bounds__(NT + 32) k_step_ilv_batched(const VDom *__restrict__ doms,
+                                                               const Tile *__restrict__ tiles,
+                                                               int ntiles, int parity, int stages,
+                                                               int *status) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    ilv_run<9, NT, CPT, VEC>(IlvBatchCursor(doms, tiles, (int)blockIdx.x, (int)gridDim.x, parity),
+                             status, ntiles, stages, smem);
 }
 
 template <int Q, int NT, int CPT, bool VEC>
@@ -833,12 +897,48 @@ static cudaError_t launch_ring_batched_t(const VDom *doms, const Tile *strips, i
     return cudaGetLastError();
 }
 
+template <int NT, int CPT, bool VEC>
+static cudaError_t launch_ilv_batched_t(const VDom *doms, const Tile *tiles, int ntiles, int parity,
+                                        int stages, int *status, cudaStream_t stream) {
+    constexpr int TW = NT * CPT;
+    const size_t smem = kBarBytes + (size_t)stages * 12 * (TW + 8) * sizeof(float);
+    if (stages < 2 || stages > kBarBytes / 16 || smem > 227 * 1024 || ntiles < 1)
+        return cudaErrorInvalidValue;
+    auto kern = k_step_ilv_batched<NT, CPT, VEC>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT + 32, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    long long grid = (long long)sms * occ;
+    if (grid > ntiles) grid = ntiles;
+    kern<<<(unsigned)grid, NT + 32, smem, stream>>>(doms, tiles, ntiles, parity, stages, status);
+    return cudaGetLastError();
+}
+
 // kind 2: ring strips; 4: the same, warp-specialised; 5: warp-specialised with
 // 4 contiguous cells per thread
 cudaError_t launch_ring_batched(const VDom *doms, const Tile *strips, int nstrips, int parity,
-                                Launch L, cudaStream_t stream) {
+                                Launch L, int *status, cudaStream_t stream) {
     const int nt = 32 * L.warps;
     const int st = L.rows;
+    if (L.kind == 6) {     // interleaved tile table, strided cells
+        if (nt == 128 && L.cpt == 2)
+            return launch_ilv_batched_t<128, 2, false>(doms, strips, nstrips, parity, st, status, stream);
+        if (nt == 256 && L.cpt == 2)
+            return launch_ilv_batched_t<256, 2, false>(doms, strips, nstrips, parity, st, status, stream);
+        return cudaErrorInvalidValue;
+    }
+    if (L.kind == 7) {     // interleaved tile table, 4 consecutive cells
+        if (nt == 64 && L.cpt == 4)
+            return launch_ilv_batched_t<64, 4, true>(doms, strips, nstrips, parity, st, status, stream);
+        if (nt == 128 && L.cpt == 4)
+            return launch_ilv_batched_t<128, 4, true>(doms, strips, nstrips, parity, st, status, stream);
+        return cudaErrorInvalidValue;
+    }
     if (L.kind == 5) {
         if (nt == 64 && L.cpt == 4)
             return launch_ring_batched_t<64, 4, true, true>(doms, strips, nstrips, parity, st, stream);

@@ -41,7 +41,8 @@ def test_batched_matches_oracle_per_domain():
 @pytest.mark.parametrize("L", [Launch(1, 2, 1), Launch(2, 1, 2), Launch(4, 4, 1), Launch(4, 2, 2),
                                Launch(4, 4, 3, 2), Launch(2, 8, 2, 2), Launch(1, 8, 3, 2),
                                Launch(2, 8, 2, 4), Launch(1, 8, 3, 4), Launch(4, 4, 4, 5),
-                               Launch(4, 2, 2, 5)])
+                               Launch(4, 2, 2, 5), Launch(2, 4, 2, 6), Launch(2, 8, 3, 6),
+                               Launch(4, 4, 4, 7), Launch(4, 2, 3, 7)])
 def test_batched_launch_shapes(L):
     torch = torch_cuda()
     doms = W.batched_channels(n=4, seed=43, nx_range=(20, 300), ny_range=(4, 40))
@@ -55,7 +56,8 @@ def test_batched_launch_shapes(L):
         assert np.abs(f - f_o).max() <= 5e-7, (L, d)
 
 
-@pytest.mark.parametrize("L", [Launch(4, 4, 1), Launch(4, 4, 3, 2), Launch(4, 4, 4, 5)])
+@pytest.mark.parametrize("L", [Launch(4, 4, 1), Launch(4, 4, 3, 2), Launch(4, 4, 4, 5),
+                               Launch(4, 4, 4, 7)])
 def test_batched_equals_single_domain_solver(L):
     """The batched kernels and the single-domain kernels run the same per-cell
     arithmetic (the compiler may contract a multiply-add differently in the two
