@@ -77,6 +77,16 @@ typedef struct {
                        population that bounces off it gains 2 w_i eps rho_w (e_i.u_w)/cs^2
                        with rho_w = 1 (moving-wall bounce-back with the eps-weighted
                        equilibrium of Eq. d2q9eq).  All zero: resting walls.         */
+    int wall_kind;  /* the y walls (bit1 of wall_mask): 0 half-way bounce-back, the
+                       walls half a cell outside rows 0 and ny-1 (H = ny); 1 the
+                       non-equilibrium extrapolation scheme the paper's validation
+                       runs use (Sec. "Examples and discussions"): rows 0 and ny-1
+                       are nodes on the plates (H = ny - 1); each takes
+                       f^eq(eps, rho, u_plate) plus the non-equilibrium part of its
+                       fluid neighbour and relaxes with no source term; u_plate = 0
+                       below and u_wall above.  Needs ny >= 3, no z walls; the
+                       single-domain solver only (vans_batch_* and the adjoint
+                       answer VANS_ERR_UNSUPPORTED).                                 */
 } vans_params;
 
 /* Launch configuration of the step kernels (chosen by vans_autotune).

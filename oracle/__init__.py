@@ -57,7 +57,7 @@ class _Params(ctypes.Structure):
         ("tau", ctypes.c_double), ("g", ctypes.c_double * 3),
         ("drag_mode", ctypes.c_int), ("k_mode", ctypes.c_int),
         ("d_p", ctypes.c_double), ("K", ctypes.c_double), ("F_eps", ctypes.c_double),
-        ("u_wall", ctypes.c_double * 3),
+        ("u_wall", ctypes.c_double * 3), ("wall_kind", ctypes.c_int),
     ]
 
 
@@ -77,6 +77,7 @@ class Params:
     K: float = 1.0
     F_eps: float = 0.0
     u_wall: tuple = (0.0, 0.0, 0.0)
+    wall_kind: int = 0
 
     def _c(self) -> _Params:
         g = tuple(float(v) for v in self.g) + (0.0,) * (3 - len(self.g))
@@ -84,7 +85,8 @@ class Params:
         return _Params(int(self.q), int(self.nx), int(self.ny), int(self.nz),
                        int(self.wall_mask), float(self.tau), (ctypes.c_double * 3)(*g),
                        int(self.drag_mode), int(self.k_mode), float(self.d_p),
-                       float(self.K), float(self.F_eps), (ctypes.c_double * 3)(*uw))
+                       float(self.K), float(self.F_eps), (ctypes.c_double * 3)(*uw),
+                       int(self.wall_kind))
 
     @property
     def dim(self) -> int:

@@ -43,6 +43,18 @@
  *   R7  Walls are half-way bounce-back: a population that would leave through a
  *       wall face returns to its node in the opposite direction after one step.
  *   R8  nu = cs^2 (tau - 1/2) dt, p = cs^2 rho (stated after Eq. VNS2), dt = 1.
+ *   R9  wall_kind 1 (the paper's validation runs, Sec. "Examples and
+ *       discussions", apply the non-equilibrium extrapolation scheme of Guo,
+ *       Zheng & Shi 2002 at both plates): the rows y = 0 and y = ny-1 are nodes
+ *       on the plates (H = ny - 1).  A plate node x_b takes
+ *         f_i(x_b) = f_i^eq(eps(x_b), rho(x_f), u_b)
+ *                    + [f_i(x_f) - f_i^eq(eps(x_f), rho(x_f), u(x_f))]
+ *       from its fluid neighbour x_f = x_b +- e_y (rho, u by Eqs. 0moment and
+ *       1moment), u_b = 0 on the lower plate and u_wall on the upper one, and
+ *       relaxes towards f^eq(eps(x_b), rho_b, u_b) with no source term (the
+ *       plate velocity is imposed, the drag acts on the fluid).  The paper does
+ *       not say how the forcing terms meet the boundary nodes; this is the
+ *       reading.  Only the y walls take this scheme (no z walls).
  *
  * Layout: f[i*N + n], n = (z*ny + y)*nx + x, N = nx*ny*nz.  eps is double[N].
  */
@@ -63,7 +75,9 @@ typedef struct {
     int k_mode;         /* 0 Ergun K(eps,d_p), F_eps(eps); 1 fixed K, F_eps;
                            2 fixed K, F_eps(eps) from the paper's formula          */
     double d_p, K, F_eps;
-    double u_wall[3];   /* velocity of the upper y wall (moving-wall bounce-back)  */
+    double u_wall[3];   /* velocity of the upper y wall                            */
+    int wall_kind;      /* y walls: 0 half-way bounce-back (R7), 1 non-equilibrium
+                           extrapolation at nodes on the plates (R9)               */
 } or_params;
 
 static const double CS2 = 1.0 / 3.0;
@@ -142,7 +156,15 @@ static int check_params(const or_params *p, lattice_t *L)
     if (p->nx < 1 || p->ny < 1 || p->nz < 1) return -1;
     if (p->q == 9 && p->nz != 1) return -1;
     if (!(p->tau > 0.5)) return -1;
+    if (p->wall_kind != 0 && p->wall_kind != 1) return -1;
+    if (p->wall_kind == 1 && (!(p->wall_mask & 2) || (p->wall_mask & 5) || p->ny < 3)) return -1;
     return 0;
+}
+
+/* R9: is row y a plate node? */
+static inline int plate_row(const or_params *p, int y)
+{
+    return p->wall_kind == 1 && (y == 0 || y == p->ny - 1);
 }
 
 static double nu_of(const or_params *p) { return CS2 * (p->tau - 0.5); } /* R8 */
@@ -343,7 +365,33 @@ static void gather_cell(const lattice_t *L, const double *f, long N, long n, dou
     for (int i = 0; i < L->q; ++i) fc[i] = f[i * N + n];
 }
 
-/* Initial state of the validation runs: rho = 1, u = 0, so f_i = w_i eps. */
+/* R9: populations of the plate nodes from their fluid neighbours. */
+static void plate_nodes(const or_params *p, const lattice_t *L, const double *eps,
+                        const double *grad, double *f)
+{
+    if (p->wall_kind != 1) return;
+    const int nx = p->nx, ny = p->ny, nz = p->nz;
+    const long N = (long)nx * ny * nz;
+    for (int z = 0; z < nz; ++z)
+        for (int side = 0; side < 2; ++side) {
+            const int yb = side ? ny - 1 : 0, yf = side ? ny - 2 : 1;
+            const double zero[3] = {0, 0, 0};
+            const double *ub = side ? p->u_wall : zero;
+            for (int x = 0; x < nx; ++x) {
+                const long nb_ = ((long)z * ny + yb) * nx + x, nf = ((long)z * ny + yf) * nx + x;
+                double fc[19], feqf[19], feqb[19], gc[3] = {grad[nf], grad[N + nf], grad[2 * N + nf]};
+                cell_t c;
+                gather_cell(L, f, N, nf, fc);
+                cell_moments(p, L, fc, eps[nf], gc, &c);
+                equilibrium(L, eps[nf], c.rho, c.u, feqf);
+                equilibrium(L, eps[nb_], c.rho, ub, feqb);
+                for (int i = 0; i < L->q; ++i) f[i * N + nb_] = feqb[i] + (fc[i] - feqf[i]);
+            }
+        }
+}
+
+/* Initial state of the validation runs: rho = 1, u = 0, so f_i = w_i eps (and
+ * the plate nodes from their neighbours under R9). */
 int or_init(const or_params *p, const double *eps, double *f)
 {
     lattice_t L;
@@ -351,6 +399,13 @@ int or_init(const or_params *p, const double *eps, double *f)
     const long N = (long)p->nx * p->ny * p->nz;
     for (int i = 0; i < L.q; ++i)
         for (long n = 0; n < N; ++n) f[i * N + n] = L.w[i] * eps[n];
+    if (p->wall_kind == 1) {
+        double *grad = (double *)malloc(sizeof(double) * 3 * N);
+        if (!grad) return -2;
+        grad_eps_field(p, &L, eps, grad);
+        plate_nodes(p, &L, eps, grad, f);
+        free(grad);
+    }
     return 0;
 }
 
@@ -387,6 +442,16 @@ static void collide(const or_params *p, const lattice_t *L, const double *eps, c
         double fc[19], feq[19], S[19], gc[3] = {grad[n], grad[N + n], grad[2 * N + n]};
         cell_t c;
         gather_cell(L, f, N, n, fc);
+        const int y = (int)((n / p->nx) % p->ny);
+        if (plate_row(p, y)) {
+            /* R9: relax towards the plate's equilibrium, no source term */
+            const double zero[3] = {0, 0, 0};
+            double R = 0;
+            for (int i = 0; i < L->q; ++i) R += fc[i];
+            equilibrium(L, eps[n], R / eps[n], y == 0 ? zero : p->u_wall, feq);
+            for (int i = 0; i < L->q; ++i) f[i * N + n] = fc[i] - (fc[i] - feq[i]) / tau;
+            continue;
+        }
         cell_moments(p, L, fc, eps[n], gc, &c);
         equilibrium(L, eps[n], c.rho, c.u, feq);
         source_term(L, tau, c.u, c.V, S);   /* P_i + F_i in one call: V = p grad eps + F */
@@ -416,7 +481,7 @@ static void stream(const or_params *p, const lattice_t *L, const double *eps, co
                     const int zd = nb(z, L->e[i][2], nz, wz);
                     if (xd < 0 || yd < 0 || zd < 0) {
                         double add = 0;
-                        if (yd < 0 && L->e[i][1] > 0 && xd >= 0 && zd >= 0) {
+                        if (p->wall_kind == 0 && yd < 0 && L->e[i][1] > 0 && xd >= 0 && zd >= 0) {
                             const double eu = L->e[i][0] * p->u_wall[0] + L->e[i][1] * p->u_wall[1] +
                                               L->e[i][2] * p->u_wall[2];
                             add = 2.0 * L->w[i] * eps[n] * eu / CS2;
@@ -463,10 +528,12 @@ int or_run(const or_params *p, const double *eps, double *f, int nsteps)
     if (!grad || !tmp) { free(grad); free(tmp); return -2; }
     grad_eps_field(p, &L, eps, grad);
     for (int t = 0; t < nsteps; ++t) {
+        plate_nodes(p, &L, eps, grad, f);     /* R9 (no-op for bounce-back walls) */
         collide(p, &L, eps, grad, f);
         stream(p, &L, eps, f, tmp);
         memcpy(f, tmp, sizeof(double) * L.q * N);
     }
+    plate_nodes(p, &L, eps, grad, f);
     free(grad);
     free(tmp);
     return 0;
@@ -645,7 +712,7 @@ static void stream_transpose(const or_params *p, const lattice_t *L, const doubl
                         const double lb = lam[L->opp[i] * N + n];
                         mu[i * N + n] = lb;
                         /* moving-wall term -2 w_i eps (e_i.u_w)/cs2 depends on eps(x) */
-                        if (yd < 0 && L->e[i][1] > 0 && xd >= 0 && zd >= 0) {
+                        if (p->wall_kind == 0 && yd < 0 && L->e[i][1] > 0 && xd >= 0 && zd >= 0) {
                             const double eu = L->e[i][0] * p->u_wall[0] + L->e[i][1] * p->u_wall[1] +
                                               L->e[i][2] * p->u_wall[2];
                             epsbar[n] += -2.0 * L->w[i] * eu / CS2 * lb;
@@ -665,6 +732,7 @@ int or_adjoint(const or_params *p, const double *eps, int nsteps, int x_out, dou
     lattice_t L;
     if (check_params(p, &L)) return -1;
     if (x_out < 0 || x_out >= p->nx || nsteps < 0) return -1;
+    if (p->wall_kind != 0) return -1;    /* the adjoint covers bounce-back walls only */
     const int Q = L.q;
     const long N = (long)p->nx * p->ny * p->nz;
     double *traj = (double *)malloc(sizeof(double) * Q * N * ((long)nsteps + 1));

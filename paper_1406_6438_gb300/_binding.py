@@ -33,6 +33,7 @@ class _CParams(ctypes.Structure):
         ("wall_mask", ctypes.c_int), ("tau", ctypes.c_float), ("g", ctypes.c_float * 3),
         ("drag_mode", ctypes.c_int), ("k_mode", ctypes.c_int), ("d_p", ctypes.c_float),
         ("K", ctypes.c_float), ("F_eps", ctypes.c_float), ("u_wall", ctypes.c_float * 3),
+        ("wall_kind", ctypes.c_int),
     ]
 
 
@@ -57,6 +58,7 @@ class Params:
     K: float = 1.0
     F_eps: float = 0.0
     u_wall: tuple = (0.0, 0.0, 0.0)
+    wall_kind: int = 0
 
     @classmethod
     def of(cls, p) -> "Params":
@@ -68,7 +70,7 @@ class Params:
         return _CParams(int(self.q), int(self.nx), int(self.ny), int(self.nz), int(self.wall_mask),
                         float(self.tau), (ctypes.c_float * 3)(*g), int(self.drag_mode),
                         int(self.k_mode), float(self.d_p), float(self.K), float(self.F_eps),
-                        (ctypes.c_float * 3)(*uw))
+                        (ctypes.c_float * 3)(*uw), int(self.wall_kind))
 
     @property
     def dim(self) -> int:

@@ -52,6 +52,13 @@ int validate(const vans_params *p, bool batched) {
         if (!isfinite(p->g[k]) || !isfinite(p->u_wall[k])) return VANS_ERR_ARG;
     const bool moving = p->u_wall[0] != 0.f || p->u_wall[1] != 0.f || p->u_wall[2] != 0.f;
     if (moving && !(p->wall_mask & 2)) return VANS_ERR_ARG;     // the plate is a y wall
+    if (p->wall_kind != 0 && p->wall_kind != 1) return VANS_ERR_ARG;
+    if (p->wall_kind == 1) {
+        // plates on nodes: y walls only, at least one fluid row between them
+        if (!(p->wall_mask & 2) || p->ny < 3) return VANS_ERR_ARG;
+        if ((p->wall_mask & 4) || batched) return VANS_ERR_UNSUPPORTED;
+        return VANS_ERR_UNSUPPORTED;   // kernels not yet built
+    }
     if (p->drag_mode < 0 || p->drag_mode > 2) return VANS_ERR_ARG;
     if (p->k_mode < 0 || p->k_mode > 2) return VANS_ERR_ARG;
     if (p->drag_mode != 0) {

@@ -49,13 +49,13 @@ def uniform_eps(shape, value: float) -> np.ndarray:
 
 
 def params(q=9, nx=1, ny=1, nz=1, wall_mask=0, tau=0.8, g=(0.0, 0.0, 0.0), drag_mode=0,
-           k_mode=0, d_p=1.0, K=1.0, F_eps=0.0, u_wall=(0.0, 0.0, 0.0)) -> dict:
+           k_mode=0, d_p=1.0, K=1.0, F_eps=0.0, u_wall=(0.0, 0.0, 0.0), wall_kind=0) -> dict:
     """A parameter set (the fields of ``vans_params``), floats rounded to float32."""
     g = tuple(f32(v) for v in g) + (0.0,) * (3 - len(g))
     uw = tuple(f32(v) for v in u_wall) + (0.0,) * (3 - len(u_wall))
     return dict(q=int(q), nx=int(nx), ny=int(ny), nz=int(nz), wall_mask=int(wall_mask),
                 tau=f32(tau), g=g, drag_mode=int(drag_mode), k_mode=int(k_mode),
-                d_p=f32(d_p), K=f32(K), F_eps=f32(F_eps), u_wall=uw)
+                d_p=f32(d_p), K=f32(K), F_eps=f32(F_eps), u_wall=uw, wall_kind=int(wall_kind))
 
 
 # --------------------------------------------------------------------------
@@ -123,18 +123,22 @@ def adjoint_channel(nx: int = 512, ny: int = 512, seed: int = 5, nsteps: int = 2
     return p, smoothed_noise((1, ny, nx), 16.0, 0.4, 1.0, seed), nsteps, every
 
 
-def couette_80(Re: float = 1.0, Da: float = 1e-2, eps: float = 0.1, n: int = 80, nx: int = 80):
+def couette_80(Re: float = 1.0, Da: float = 1e-2, eps: float = 0.1, n: int = 80, nx: int = 80,
+               wall_kind: int = 0):
     """The paper's validation case: Couette flow through a porous medium of
     uniform porosity eps = 0.1 between plates H = L = 80 apart, the upper plate
     moving at u0 (the characteristic velocity), periodic in x; tau = 0.6574 at
     Re = 50, 0.8 otherwise; rho = 1, u = 0 at start; Re = L u0 / nu, Da = K / L^2;
-    drag law with K = Da L^2 and F_eps = 1.75/sqrt(150 eps^3); no body force."""
+    drag law with K = Da L^2 and F_eps = 1.75/sqrt(150 eps^3); no body force.
+    wall_kind 0: half-way bounce-back plates, n rows of nodes; wall_kind 1: the
+    non-equilibrium extrapolation scheme with the plates on nodes, n + 1 rows."""
     tau = 0.6574 if Re == 50 else 0.8
     nu = (f32(tau) - 0.5) / 3.0
     u0 = Re * nu / n
-    p = params(q=9, nx=nx, ny=n, wall_mask=2, tau=tau, drag_mode=2, k_mode=2, K=Da * n * n,
-               u_wall=(u0, 0.0, 0.0))
-    return p, uniform_eps((1, n, nx), eps)
+    ny = n + 1 if wall_kind == 1 else n
+    p = params(q=9, nx=nx, ny=ny, wall_mask=2, tau=tau, drag_mode=2, k_mode=2, K=Da * n * n,
+               u_wall=(u0, 0.0, 0.0), wall_kind=wall_kind)
+    return p, uniform_eps((1, ny, nx), eps)
 
 
 def fd_cells(shape, count: int = 32, seed: int = 5):

@@ -211,3 +211,80 @@ def test_porous_couette_of_the_paper_against_bvp():
     ref = np.interp(np.arange(80) + 0.5, yb, ub)
     assert np.abs(u[0, 0, :, 0] - ref).max() <= 2e-3 * u0
     assert 0.9 < u[0, 0, -1, 0] / u0 < 1.0
+
+
+# ---- non-equilibrium extrapolation at nodes on the plates (wall_kind 1) ----
+
+@pytest.mark.parametrize("tau", [0.6, 0.8, 1.3])
+def test_couette_exactly_linear_with_nee_plates(tau):
+    """eps = 1, no drag, plates on the nodes y = 0 and y = H = ny - 1 with the
+    non-equilibrium extrapolation scheme: plane Couette flow is linear at every
+    node, u(y) = u0 y / H, for any tau (the non-equilibrium part of a linear
+    profile is uniform, so extrapolating it from the neighbour is exact)."""
+    H, u0 = 8, 1e-3
+    p = O.Params(q=9, nx=2, ny=H + 1, wall_mask=2, tau=tau, u_wall=(u0, 0, 0), wall_kind=1)
+    eps = np.ones(p.shape)
+    f = O.run(p, eps, O.init(p, eps), 6000)
+    rho, u = O.moments(p, eps, f)
+    y = np.arange(H + 1)
+    assert np.abs(u[0, 0, :, 0] - u0 * y / H).max() <= 1e-10 * u0
+    assert np.abs(u[1]).max() <= 1e-10 * u0
+    assert np.abs(rho - 1).max() <= 1e-10
+
+
+def test_poiseuille_with_nee_plates_is_parabolic_plus_a_uniform_slip():
+    """Force-driven channel between resting NEE plates: in the bulk the
+    lattice reproduces the parabola g/(2 nu) y (H - y) exactly; the boundary
+    closure adds one uniform offset c(tau) g/nu on the fluid nodes, the same for
+    every H (so the relative error falls as H^-2)."""
+    tau, g = 0.8, 1e-6
+    nu = CS2 * (tau - 0.5)
+    offs = []
+    for H in (8, 16):
+        p = O.Params(q=9, nx=2, ny=H + 1, wall_mask=2, tau=tau, g=(g, 0, 0), wall_kind=1)
+        eps = np.ones(p.shape)
+        f = O.run(p, eps, O.init(p, eps), int(40 * H * H / nu))
+        _, u = O.moments(p, eps, f)
+        y = np.arange(H + 1)
+        d = (u[0, 0, :, 0] - g / (2 * nu) * y * (H - y)) / (g / nu)
+        assert abs(d[0]) <= 1e-9 and abs(d[-1]) <= 1e-9          # plates at rest
+        assert np.ptp(d[1:-1]) <= 1e-9                             # uniform offset
+        offs.append(d[1])
+    assert abs(offs[0] - offs[1]) <= 1e-8
+    assert 0.0 < abs(offs[0]) < 1.0
+
+
+@pytest.mark.parametrize("Re,Da,steps", [(1, 1e-3, 30000), (50, 1e-2, 120000)])
+def test_porous_couette_with_nee_plates_against_bvp(Re, Da, steps):
+    """The paper's validation case with the boundary scheme it names
+    (non-equilibrium extrapolation on both plates): 81 nodes across, so the
+    plates are H = 80 apart; eps = 0.1.  Steady profile against the 4001-point
+    Newton solution of the paper's equation with u(0) = 0, u(H) = u0, at every
+    node, within 0.4 % of u0."""
+    p, eps32 = W.couette_80(Re=Re, Da=Da, nx=1, wall_kind=1)
+    H = 80
+    assert p["ny"] == H + 1
+    e = eps32.astype(np.float64)
+    po = O.Params(**p)
+    f = O.run(po, e, O.init(po, e), steps)
+    _, u = O.moments(po, e, f)
+    nu = CS2 * (p["tau"] - 0.5)
+    ee = float(eps32.flat[0])
+    Feps = 1.75 / np.sqrt(150 * ee ** 3)
+    u0 = p["u_wall"][0]
+    yb, ub = porous_bvp(nu, ee, p["K"], Feps, 0.0, H, u_top=u0)
+    ref = np.interp(np.arange(H + 1), yb, ub)
+    assert np.abs(u[0, 0, :, 0] - ref).max() <= 4e-3 * u0
+
+
+def test_nee_parameters_validated():
+    eps = np.ones((1, 5, 4))
+    for bad in (dict(wall_mask=0), dict(wall_mask=3), dict(ny=2), dict(wall_kind=2)):
+        kw = dict(q=9, nx=4, ny=5, wall_mask=2, tau=0.8, wall_kind=1)
+        kw.update(bad)
+        p = O.Params(**kw)
+        with pytest.raises(Exception):
+            O.init(p, np.ones(p.shape))
+    p = O.Params(q=9, nx=4, ny=5, wall_mask=2, tau=0.8, wall_kind=1)
+    with pytest.raises(Exception):
+        O.adjoint(p, eps, 3, 3)
