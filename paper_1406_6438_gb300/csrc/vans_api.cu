@@ -57,7 +57,6 @@ int validate(const vans_params *p, bool batched) {
         // plates on nodes: y walls only, at least one fluid row between them
         if (!(p->wall_mask & 2) || p->ny < 3) return VANS_ERR_ARG;
         if ((p->wall_mask & 4) || batched) return VANS_ERR_UNSUPPORTED;
-        return VANS_ERR_UNSUPPORTED;   // kernels not yet built
     }
     if (p->drag_mode < 0 || p->drag_mode > 2) return VANS_ERR_ARG;
     if (p->k_mode < 0 || p->k_mode > 2) return VANS_ERR_ARG;
@@ -107,7 +106,9 @@ void fill_dom(const vans_params *p, VDom &d) {
     d.uw[0] = p->u_wall[0];
     d.uw[1] = p->u_wall[1];
     d.uw[2] = (p->q == 19) ? p->u_wall[2] : 0.f;
-    d.moving = (d.uw[0] != 0.f || d.uw[1] != 0.f || d.uw[2] != 0.f) ? 1 : 0;
+    d.nee = (p->wall_kind == 1) ? 1 : 0;
+    // the bounce-back gain of a moving wall; plates on nodes impose u_wall directly
+    d.moving = (!d.nee && (d.uw[0] != 0.f || d.uw[1] != 0.f || d.uw[2] != 0.f)) ? 1 : 0;
 }
 
 bool launch_ok(const vans_launch *c, int q, bool batched) {
@@ -510,6 +511,7 @@ int vans_step_monitored(vans_t h, int nsteps, int every, float *rho_dev, float *
                         float *stats_dev) {
     if (!h || h->batched || nsteps < 0 || every < 1 || !rho_dev || !u_dev || !stats_dev)
         return VANS_ERR_ARG;
+    if (h->dom.nee) return VANS_ERR_UNSUPPORTED;    // plates on nodes: use vans_moments
     if (!h->eps_set) return VANS_ERR_STATE;
     if (cudaMemsetAsync(stats_dev, 0, 4 * sizeof(float), h->stream) != cudaSuccess)
         return VANS_ERR_CUDA;
@@ -586,6 +588,9 @@ int vans_get_launch(vans_t h, vans_launch *cfg) {
 
 int vans_set_launch(vans_t h, const vans_launch *cfg) {
     if (!h || !launch_ok(cfg, h->q, h->batched)) return VANS_ERR_ARG;
+    if (!h->batched && h->dom.nee && !vans::launch_has_plates(h->q, Launch{cfg->cpt, cfg->warps,
+                                                                          cfg->rows, cfg->kind}))
+        return VANS_ERR_UNSUPPORTED;
     const Launch L{cfg->cpt, cfg->warps, cfg->rows, cfg->kind};
     if (h->batched) return set_batch_launch(h, L);
     h->L = L;
@@ -605,6 +610,7 @@ int vans_autotune(vans_t h, vans_launch *chosen) {
     float *outb = h->st[h->cur ^ 1];
     const int reps = h->dom.cells > (1 << 22) ? 5 : 20;
     for (const Launch &L : cs) {
+        if (h->dom.nee && !vans::launch_has_plates(h->q, L)) continue;   // no plate instance
         const float ms = time_launches(
             h, [&] { vans::launch_step(h->q, h->dom, in, outb, L, h->stream); }, reps);
         h->launches += 3 * reps + 2;
@@ -636,6 +642,7 @@ int vans_flux(vans_t h, const float *state, int x_out, float *J_dev) {
 
 int vans_flux_seed(vans_t h, const float *state, int x_out, float *lam_dev, float *grad_acc) {
     if (!h || h->batched || !lam_dev || !grad_acc) return VANS_ERR_ARG;
+    if (h->dom.nee) return VANS_ERR_UNSUPPORTED;    // the adjoint covers bounce-back walls
     if (!h->eps_set) return VANS_ERR_STATE;
     if (x_out < 0 || x_out >= h->dom.nx) return VANS_ERR_ARG;
     const int D = h->q == 9 ? 2 : 3;
@@ -653,6 +660,7 @@ int vans_step_adjoint(vans_t h, const float *state_t, const float *lam_in, float
                       float *grad_acc) {
     if (!h || h->batched || !state_t || !lam_in || !lam_out || !grad_acc) return VANS_ERR_ARG;
     if (lam_in == lam_out || (const float *)lam_out == state_t) return VANS_ERR_ARG;
+    if (h->dom.nee) return VANS_ERR_UNSUPPORTED;
     if (!h->eps_set) return VANS_ERR_STATE;
     ++h->launches;
     return cuda_status(vans::launch_step_adjoint(h->q, h->dom, state_t, lam_in, lam_out, grad_acc,
@@ -662,6 +670,7 @@ int vans_step_adjoint(vans_t h, const float *state_t, const float *lam_in, float
 int vans_adjoint_segment(vans_t h, const float *ckpt, float *seg, int len, float *lam, float *tmp,
                          float *grad_acc) {
     if (!h || h->batched || !ckpt || !seg || !lam || !tmp || !grad_acc || len < 1) return VANS_ERR_ARG;
+    if (h->dom.nee) return VANS_ERR_UNSUPPORTED;
     if (lam == tmp) return VANS_ERR_ARG;
     if (!h->eps_set) return VANS_ERR_STATE;
     const long long sf = h->sfloats;

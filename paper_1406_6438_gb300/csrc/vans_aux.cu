@@ -58,6 +58,32 @@ __device__ __forceinline__ void cell_xyz(const VDom &d, long long n, int &x, int
     z = (int)(r / d.ny);
 }
 
+// Populations (as deviations from w_i eps(x)) that cell (x,y,z) holds before
+// its collision: pulled from the state, or, for a plate node (wall_kind 1),
+// f^eq(eps_b, rho_f, u_b) plus its fluid neighbour's non-equilibrium part.
+template <int Q>
+__device__ __forceinline__ void cell_state(const VDom &d, const float *__restrict__ st, int x, int y,
+                                           int z, const Nb3 &Y, const Nb3 &Z, float h[Q]) {
+    if (d.nee && (y == 0 || y == d.ny - 1)) {
+        const int yf = (y == 0) ? 1 : d.ny - 2;
+        Nb3 Yf, Zf;
+        nb_yz<Q>(d, yf, z, Yf, Zf);
+        float hf[Q], ef, etf[Q];
+        pull_cell<Q>(d, st, x, yf, z, Yf, Zf, hf);
+        eps_cell<Q>(d, x, yf, z, Yf, Zf, ef, etf);
+        Macro<Q> M;
+        macro<Q>(d, hf, ef, etf, M);
+        const float eb = d.eps[row_offset(d, y, z) + x];
+        const float zero[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+            h[i] = plate_value<Q>(d, i, hf[i], M, eb, eb, y == 0 ? zero : d.uw, 1.f);
+        return;
+    }
+    pull_cell<Q>(d, st, x, y, z, Y, Z, h);
+    apply_moving_wall<Q>(d, Y.wall[2], Z, d.eps[row_offset(d, y, z) + x], h);
+}
+
 // --------------------------------------------------------------- S8 -----
 // rho and u of the current state (Eqs. 0moment and 1moment, drag in closed form)
 template <int Q>
@@ -71,9 +97,8 @@ __global__ void k_moments(const VDom d, const float *__restrict__ st, float *__r
         Nb3 Y, Z;
         nb_yz<Q>(d, y, z, Y, Z);
         float h[Q], e0, et[Q];
-        pull_cell<Q>(d, st, x, y, z, Y, Z, h);
+        cell_state<Q>(d, st, x, y, z, Y, Z, h);
         eps_cell<Q>(d, x, y, z, Y, Z, e0, et);
-        apply_moving_wall<Q>(d, Y.wall[2], Z, e0, h);
         Macro<Q> M;
         macro<Q>(d, h, e0, et, M);
         if (rho) rho[n] = M.rho;
@@ -96,8 +121,7 @@ __global__ void k_export(const VDom d, const float *__restrict__ st, float *__re
         nb_yz<Q>(d, y, z, Y, Z);
         const float e0 = d.eps[row_offset(d, y, z) + x];
         float h[Q];
-        pull_cell<Q>(d, st, x, y, z, Y, Z, h);
-        apply_moving_wall<Q>(d, Y.wall[2], Z, e0, h);
+        cell_state<Q>(d, st, x, y, z, Y, Z, h);
 #pragma unroll
         for (int i = 0; i < Q; ++i) f[i * d.cells + n] = h[i] + L::w(i) * e0;
     }
@@ -208,9 +232,8 @@ __global__ void k_check(const VDom d, const float *__restrict__ st, int *flag) {
         Nb3 Y, Z;
         nb_yz<Q>(d, y, z, Y, Z);
         float h[Q], e0, et[Q];
-        pull_cell<Q>(d, st, x, y, z, Y, Z, h);
+        cell_state<Q>(d, st, x, y, z, Y, Z, h);
         eps_cell<Q>(d, x, y, z, Y, Z, e0, et);
-        apply_moving_wall<Q>(d, Y.wall[2], Z, e0, h);
         Macro<Q> M;
         macro<Q>(d, h, e0, et, M);
         if (!isfinite(M.R) || !isfinite(M.un) || !(M.un < 0.5f)) atomicOr(flag, 1);
@@ -241,9 +264,8 @@ __global__ void __launch_bounds__(256) k_flux(const VDom d, const float *__restr
         Nb3 Y, Z;
         nb_yz<Q>(d, y, z, Y, Z);
         float h[Q], e0, et[Q];
-        pull_cell<Q>(d, st, x_out, y, z, Y, Z, h);
+        cell_state<Q>(d, st, x_out, y, z, Y, Z, h);
         eps_cell<Q>(d, x_out, y, z, Y, Z, e0, et);
-        apply_moving_wall<Q>(d, Y.wall[2], Z, e0, h);
         Macro<Q> M;
         macro<Q>(d, h, e0, et, M);
         acc += M.R * M.u[0];

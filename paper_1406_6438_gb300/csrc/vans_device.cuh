@@ -411,11 +411,12 @@ __device__ __forceinline__ void macro(const VDom &d, const float h[Q], float e0,
 // and subtracting eps~_i afterwards would cost 3e-8 absolute per population.
 template <int Q>
 __device__ __forceinline__ void collide(const VDom &d, const float h[Q], float e0, const float et[Q],
-                                        float o[Q]) {
+                                        float o[Q], Macro<Q> *Mout = nullptr) {
     using L = Lat<Q>;
     constexpr int D = L::D;
     Macro<Q> M;
     macro<Q>(d, h, e0, et, M);
+    if (Mout) *Mout = M;
     const float om = d.omega, ct = d.ctau, om1 = 1.f - om;
     float uu = 0.f, uV = 0.f;
 #pragma unroll
@@ -435,6 +436,79 @@ __device__ __forceinline__ void collide(const VDom &d, const float h[Q], float e
         const float anti = 3.f * (omR * eu + ct * eV);
         o[i] = om1 * h[i] + L::w(i) * ((sym + anti) + (e0 - et[i]));
         o[j] = om1 * h[j] + L::w(j) * ((sym - anti) + (e0 - et[j]));
+    }
+}
+
+// ------------------------------------------------- plates on nodes ----
+// The non-equilibrium extrapolation scheme of the paper's validation runs
+// (wall_kind 1): rows 0 and ny-1 are nodes on the plates.  A plate node x_b
+// takes f^eq(eps_b, rho_f, u_b) plus the non-equilibrium part of its fluid
+// neighbour x_f, n_i = f_i(x_f) - f^eq_i(eps_f, rho_f, u_f), and relaxes towards
+// f^eq(eps_b, rho_f, u_b) with no source term, so its post-collision value is
+// f^eq_i(eps_b, rho_f, u_b) + (1 - omega) n_i.  From the neighbour's moments M
+// (h_i = f_i(x_f) - w_i eps_f, dl = sum h, R = eps_f rho_f) and with
+// A_i, B_i the bracket of Eq. d2q9eq minus one at u_f and at u_b,
+//   n_i = h_i - w_i (dl + R A_i),
+//   f^eq_i(eps_b, rho_f, u_b) - w_i e_ref = w_i [(eps_b - e_ref) + eps_b dl / eps_f
+//                                               + eps_b rho_f B_i],
+// all small differences, formed before any O(1) term is added.
+
+// index of the lattice direction (ex, ey, ez) (0 when there is none)
+template <int Q>
+__host__ __device__ constexpr int dir_index(int ex, int ey, int ez) {
+    for (int j = 0; j < Q; ++j)
+        if (Lat<Q>::ex(j) == ex && Lat<Q>::ey(j) == ey && Lat<Q>::ez(j) == ez) return j;
+    return 0;
+}
+
+// 3 e_i.v + 4.5 (e_i.v)^2 - 1.5 v.v
+template <int Q>
+__device__ __forceinline__ float eq_bracket(int i, const float v[3]) {
+    using L = Lat<Q>;
+    float ev = 0.f, vv = 0.f;
+    if (L::ex(i)) ev += L::ex(i) * v[0];
+    if (L::ey(i)) ev += L::ey(i) * v[1];
+    if (L::D == 3 && L::ez(i)) ev += L::ez(i) * v[2];
+#pragma unroll
+    for (int c = 0; c < L::D; ++c) vv += v[c] * v[c];
+    return 3.f * ev + 4.5f * ev * ev - 1.5f * vv;
+}
+
+// value of direction i at the plate node, minus w_i e_ref, with the neighbour's
+// non-equilibrium part scaled by keep (1 - omega: post-collision; 1: the
+// populations the node holds before its collision)
+template <int Q>
+__device__ __forceinline__ float plate_value(const VDom &d, int i, float h_i, const Macro<Q> &M,
+                                             float eb, float eref, const float ub[3], float keep) {
+    using L = Lat<Q>;
+    const float A = eq_bracket<Q>(i, M.u), B = eq_bracket<Q>(i, ub);
+    const float neq = h_i - L::w(i) * (M.dl + M.R * A);
+    (void)d;
+    return L::w(i) * ((eb - eref) + eb * M.dl * M.inv_e + eb * M.rho * B) + keep * neq;
+}
+
+// Store the inward populations of the plate nodes next to fluid row y: lo
+// (directions with e_y > 0) into row 0 when y == 1, hi (e_y < 0) into row
+// ny-1 when y == ny-2, V cells per thread from column x0, halo columns included.
+template <int Q, int V>
+__device__ __forceinline__ void store_plates(const VDom &d, float *__restrict__ fout, int y, int z,
+                                             int x0, bool plo, bool phi, const float lo[Q][V],
+                                             const float hi[Q][V]) {
+    using L = Lat<Q>;
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        if (!(side ? phi : plo)) continue;
+        const long long rb = row_offset(d, side ? y + 1 : y - 1, z);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            if (side ? L::ey(i) >= 0 : L::ey(i) <= 0) continue;
+            const float *v = side ? hi[i] : lo[i];
+            st_masked<V>(fout + i * d.plane + rb, x0, d.nx, v);
+            if (x0 == 0 && L::ex(i) < 0) fout[i * d.plane + rb + d.nx] = v[0];
+#pragma unroll
+            for (int c = 0; c < V; ++c)
+                if (x0 + c == d.nx - 1 && L::ex(i) > 0) fout[i * d.plane + rb - 1] = v[c];
+        }
     }
 }
 

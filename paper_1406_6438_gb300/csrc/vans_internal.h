@@ -28,8 +28,9 @@ struct VDom {
     long long cells;      // nx * ny * nz
     long long dense_off;  // offset of this domain in packed dense outputs (batched)
     int *status;          // device status word: bit 1 = a bounded wait timed out
-    int moving;           // 1: the upper y wall moves with velocity uw
-    float uw[3];
+    int moving;           // 1: the upper y wall moves with velocity uw (bounce-back walls)
+    float uw[3];          // velocity of the upper y wall / plate
+    int nee;              // 1: rows 0 and ny-1 are plate nodes (non-equilibrium extrapolation)
 };
 
 // One tile of the batched register-load kernel: a block-sized piece of one
@@ -58,6 +59,8 @@ cudaError_t launch_step_monitor(int q, const VDom &d, const float *fin, float *f
                                 float *u, float *stats, cudaStream_t stream);
 cudaError_t launch_step_tma(int q, const VDom &d, const float *fin, float *fout, Launch L,
                             cudaStream_t stream);
+// whether launch L has an instance for plates on nodes (wall_kind 1)
+bool launch_has_plates(int q, Launch L);
 // kinds 2, 4, 5: strip table (one CTA per strip); 6, 7: interleaved tile table
 cudaError_t launch_ring_batched(const VDom *doms, const Tile *strips, int nstrips, int parity,
                                 Launch L, int *status, cudaStream_t stream);

@@ -86,7 +86,9 @@ extern "C" int vans_step_static(const vans_params *p, const float *eps_dev, cons
     d.uw[0] = p->u_wall[0];
     d.uw[1] = p->u_wall[1];
     d.uw[2] = (p->q == 19) ? p->u_wall[2] : 0.f;
-    d.moving = (d.uw[0] != 0.f || d.uw[1] != 0.f || d.uw[2] != 0.f) ? 1 : 0;
+    d.nee = (p->wall_kind == 1) ? 1 : 0;
+    // the bounce-back gain of a moving wall; plates on nodes impose u_wall directly
+    d.moving = (!d.nee && (d.uw[0] != 0.f || d.uw[1] != 0.f || d.uw[2] != 0.f)) ? 1 : 0;
     d.eps = eps_pad;
 
     cudaStream_t s = (cudaStream_t)cuda_stream;

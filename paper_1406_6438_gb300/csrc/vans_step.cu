@@ -29,11 +29,17 @@ __device__ __forceinline__ void atomic_max_nonneg(float *a, float v) {
     atomicMax(reinterpret_cast<int *>(a), __float_as_int(v));
 }
 
-template <int Q, int CPT, bool EDGE, bool EMIT = false>
+// PL: the instance handles plates on nodes (wall_kind 1); the others carry
+// none of that code (it would raise their register count).
+template <int Q, int CPT, bool EDGE, bool EMIT = false, bool PL = false>
 __device__ __forceinline__ void step_row(const VDom &d, const float *__restrict__ fin,
                                          float *__restrict__ fout, int y, int z, int x0, int lane,
                                          const Monitor *mon = nullptr) {
     using L = Lat<Q>;
+    // plates on nodes: a plate row is written by its fluid neighbour row
+    const bool nee = PL && EDGE && d.nee;
+    if (nee && (y == 0 || y == d.ny - 1)) return;
+    const bool plo = nee && y == 1, phi = nee && y == d.ny - 2;
     const Nb3 Y = nb3<EDGE>(y, d.ny, d.wall_y);
     Nb3 Z;
     if (Q == 19) {
@@ -75,7 +81,7 @@ __device__ __forceinline__ void step_row(const VDom &d, const float *__restrict_
         }
     }
 
-    float out[Q][CPT];
+    float out[Q][CPT], lo[Q][CPT], hi[Q][CPT];   // lo / hi: the plate nodes below / above
     float dmax = 0.f, umax = 0.f;
     bool bad = false;
 #pragma unroll
@@ -109,9 +115,23 @@ __device__ __forceinline__ void step_row(const VDom &d, const float *__restrict_
             }
         }
         float o[Q];
-        collide<Q>(d, hh, e0, et, o);   // S2-S7
+        Macro<Q> M;
+        collide<Q>(d, hh, e0, et, o, nee ? &M : nullptr);   // S2-S7
 #pragma unroll
         for (int i = 0; i < Q; ++i) out[i][k] = o[i];
+        if (plo || phi) {
+            // post-collision values the plate nodes send into this row, stored
+            // against the porosity of the cell they stream to
+            const float om1 = 1.f - d.omega, zero[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const float enb = E[1][1 + L::ez(i)][k + 1 + L::ex(i)];
+                if (plo && L::ey(i) > 0)
+                    lo[i][k] = plate_value<Q>(d, i, hh[i], M, E[0][1][k + 1], enb, zero, om1);
+                if (phi && L::ey(i) < 0)
+                    hi[i][k] = plate_value<Q>(d, i, hh[i], M, E[2][1][k + 1], enb, d.uw, om1);
+            }
+        }
     }
     if (EMIT) {
         // warp maxima, one atomic per warp
@@ -146,9 +166,10 @@ __device__ __forceinline__ void step_row(const VDom &d, const float *__restrict_
                 if (L::ex(i) > 0) fout[i * d.plane + ro - 1] = out[i][k];
         }
     }
+    if (plo || phi) store_plates<Q, CPT>(d, fout, y, z, x0, plo, phi, lo, hi);
 }
 
-template <int Q, int CPT, bool EMIT = false>
+template <int Q, int CPT, bool EMIT = false, bool PL = false>
 __global__ void __launch_bounds__(256) k_step(const VDom d, const float *__restrict__ fin,
                                               float *__restrict__ fout, int nxb, Monitor mon = {}) {
     const int lane = threadIdx.x & 31;
@@ -161,11 +182,12 @@ __global__ void __launch_bounds__(256) k_step(const VDom d, const float *__restr
     if (xw >= d.nx) return;                                // whole warp
     const int x0 = xw + lane * CPT;
     const int y = r % d.ny, z = r / d.ny;
-    const bool edge = (y == 0) || (y == d.ny - 1) || (Q == 19 && (z == 0 || z == d.nz - 1));
+    const bool edge = (y == 0) || (y == d.ny - 1) || (PL && (y == 1 || y == d.ny - 2)) ||
+                      (Q == 19 && (z == 0 || z == d.nz - 1));
     if (edge)
-        step_row<Q, CPT, true, EMIT>(d, fin, fout, y, z, x0, lane, &mon);
+        step_row<Q, CPT, true, EMIT, PL>(d, fin, fout, y, z, x0, lane, &mon);
     else
-        step_row<Q, CPT, false, EMIT>(d, fin, fout, y, z, x0, lane, &mon);
+        step_row<Q, CPT, false, EMIT, PL>(d, fin, fout, y, z, x0, lane, &mon);
     if (EMIT && blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) atomicAdd(&mon.stats[3], 1.f);
 }
 
@@ -204,7 +226,10 @@ static cudaError_t launch_step_t(const VDom &d, const float *fin, float *fout, L
     const long long nblocks = (long long)nxb * nrb;
     if (nblocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     dim3 block(32 * L.warps, L.rows);
-    k_step<Q, CPT><<<(unsigned)nblocks, block, 0, stream>>>(d, fin, fout, nxb);
+    if (d.nee)
+        k_step<Q, CPT, false, true><<<(unsigned)nblocks, block, 0, stream>>>(d, fin, fout, nxb);
+    else
+        k_step<Q, CPT><<<(unsigned)nblocks, block, 0, stream>>>(d, fin, fout, nxb);
     return cudaGetLastError();
 }
 

@@ -242,15 +242,24 @@ __device__ __forceinline__ void issue_tile_ring(const VDom &d, const float *__re
 // comes in one or two aligned V-wide shared loads (8 or 16 bytes) and each
 // output row leaves in one V-wide global store.  Segment position p holds
 // column xs - 4 + p.
-template <int Q, int NT, int V, bool EDGE, class Rel>
+template <int Q, int NT, int V, bool EDGE, bool PL, class Rel>
 __device__ __forceinline__ void ring_tile_vec(const VDom &d, const float *__restrict__ sb,
                                               const float *const ey_slot[3], const Nb3 &Y,
-                                              const Nb3 &Z, float *__restrict__ fout, long long ro,
+                                              const Nb3 &Z, float *__restrict__ fout, int y, int z,
                                               int xs, int tid, Rel &&release) {
     using L = Lat<Q>;
     static_assert(V == 2 || V == 4, "2 or 4 cells per thread");
     constexpr int SEG = NT * V + 8;
     constexpr int NZ = (Q == 9) ? 1 : 3;      // z-rows per ring slot
+    // plates on nodes (PL instances only): a plate row is written by its
+    // fluid neighbour row
+    const bool nee = PL && EDGE && d.nee;
+    if (nee && (y == 0 || y == d.ny - 1)) {
+        release();
+        return;
+    }
+    const bool plo = nee && y == 1, phi = nee && y == d.ny - 2;
+    const long long ro = row_offset(d, y, z);
     const int x0l = V * tid;
     auto ywall = [&](int k) { return EDGE && Y.wall[k]; };
     auto zwall = [&](int k) { return EDGE && Z.wall[k]; };
@@ -314,7 +323,7 @@ __device__ __forceinline__ void ring_tile_vec(const VDom &d, const float *__rest
     }
     release();                  // the stage is no longer read
     constexpr int ZC = (Q == 9) ? 0 : 1;    // the z-row of dz = 0
-    float out[Q][V];
+    float out[Q][V], lo[Q][V], hi[Q][V];    // lo / hi: the plate nodes below / above
 #pragma unroll
     for (int c = 0; c < V; ++c) {
         float hh[Q], et[Q], o[Q];
@@ -326,9 +335,21 @@ __device__ __forceinline__ void ring_tile_vec(const VDom &d, const float *__rest
             et[i] = (i == 0 || wall) ? e0 : E[1 + L::ey(i)][ZC + L::ez(i)][c + 1 + L::ex(i)];
         }
         if (EDGE) apply_moving_wall<Q>(d, Y.wall[2], Z, e0, hh);
-        collide<Q>(d, hh, e0, et, o);
+        Macro<Q> M;
+        collide<Q>(d, hh, e0, et, o, nee ? &M : nullptr);
 #pragma unroll
         for (int i = 0; i < Q; ++i) out[i][c] = o[i];
+        if (plo || phi) {
+            const float om1 = 1.f - d.omega, zero[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const float enb = E[1][ZC + L::ez(i)][c + 1 + L::ex(i)];
+                if (plo && L::ey(i) > 0)
+                    lo[i][c] = plate_value<Q>(d, i, hh[i], M, E[0][ZC][c + 1], enb, zero, om1);
+                if (phi && L::ey(i) < 0)
+                    hi[i][c] = plate_value<Q>(d, i, hh[i], M, E[2][ZC][c + 1], enb, d.uw, om1);
+            }
+        }
     }
     const int x0 = xs + x0l;
 #pragma unroll
@@ -346,6 +367,7 @@ __device__ __forceinline__ void ring_tile_vec(const VDom &d, const float *__rest
                 if (L::ex(i) > 0) fout[i * d.plane + ro - 1] = out[i][c];
         }
     }
+    if (plo || phi) store_plates<Q, V>(d, fout, y, z, x0, plo, phi, lo, hi);
 }
 
 // Compute and store one staged tile of the ring pipeline (all NT threads).
@@ -353,17 +375,28 @@ __device__ __forceinline__ void ring_tile_vec(const VDom &d, const float *__rest
 // release() (the caller's way to hand the stage back to the producer), then
 // the collisions and the global stores.
 // EDGE = false: the tile's row touches no wall (the wall flags are known to be
-// false at compile time, which drops the per-direction selects).
-template <int Q, int NT, int CPT, bool VEC, bool EDGE, class Rel>
+// false at compile time, which drops the per-direction selects).  PL: the
+// instance handles plates on nodes (wall_kind 1); the others carry none of that
+// code (it would raise their register count).
+template <int Q, int NT, int CPT, bool VEC, bool EDGE, bool PL, class Rel>
 __device__ __forceinline__ void ring_tile(const VDom &d, const float *__restrict__ sb,
                                           const float *const ey_slot[3], const Nb3 &Y, const Nb3 &Z,
-                                          float *__restrict__ fout, long long ro, int xs, int tid,
+                                          float *__restrict__ fout, int y, int z, int xs, int tid,
                                           Rel &&release) {
     using L = Lat<Q>;
     constexpr int SEG = NT * CPT + 8;
     if constexpr (VEC) {
-        ring_tile_vec<Q, NT, CPT, EDGE>(d, sb, ey_slot, Y, Z, fout, ro, xs, tid, release);
+        ring_tile_vec<Q, NT, CPT, EDGE, PL>(d, sb, ey_slot, Y, Z, fout, y, z, xs, tid, release);
     } else {
+        // plates on nodes (PL instances only): a plate row is written by its
+        // fluid neighbour row
+        const bool nee = PL && EDGE && d.nee;
+        if (nee && (y == 0 || y == d.ny - 1)) {
+            release();
+            return;
+        }
+        const bool plo = nee && y == 1, phi = nee && y == d.ny - 2;
+        const long long ro = row_offset(d, y, z);
         auto ywall = [&](int k) { return EDGE && Y.wall[k]; };
         auto zwall = [&](int k) { return EDGE && Z.wall[k]; };
         float h[CPT][Q], et[CPT][Q];
@@ -391,7 +424,29 @@ __device__ __forceinline__ void ring_tile(const VDom &d, const float *__restrict
             const int x = xs + tid + cc * NT;
             float o[Q];
             if (EDGE) apply_moving_wall<Q>(d, Y.wall[2], Z, et[cc][0], h[cc]);
-            collide<Q>(d, h[cc], et[cc][0], et[cc], o);
+            Macro<Q> M;
+            collide<Q>(d, h[cc], et[cc][0], et[cc], o, nee ? &M : nullptr);
+            if (plo || phi) {
+                // eps of the plate node (the cell below / above) and of the row
+                // cells its populations stream to (x + ex, z + ez of this row),
+                // all among this cell's neighbour porosities
+                constexpr int jxp = dir_index<Q>(1, 0, 0), jxm = dir_index<Q>(-1, 0, 0);
+                constexpr int jzp = dir_index<Q>(0, 0, 1), jzm = dir_index<Q>(0, 0, -1);
+                constexpr int jym = dir_index<Q>(0, -1, 0), jyp = dir_index<Q>(0, 1, 0);
+                const float om1 = 1.f - d.omega, zero[3] = {0.f, 0.f, 0.f};
+                float lo[Q][1], hi[Q][1];
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    const int ex = L::ex(i), ez = L::ez(i);
+                    const float enb = ex > 0 ? et[cc][jxp] : ex < 0 ? et[cc][jxm]
+                                    : ez > 0 ? et[cc][jzp] : ez < 0 ? et[cc][jzm] : et[cc][0];
+                    if (plo && L::ey(i) > 0)
+                        lo[i][0] = plate_value<Q>(d, i, h[cc][i], M, et[cc][jym], enb, zero, om1);
+                    if (phi && L::ey(i) < 0)
+                        hi[i][0] = plate_value<Q>(d, i, h[cc][i], M, et[cc][jyp], enb, d.uw, om1);
+                }
+                store_plates<Q, 1>(d, fout, y, z, x, plo, phi, lo, hi);
+            }
             if (x < d.nx) {
 #pragma unroll
                 for (int i = 0; i < Q; ++i) fout[i * d.plane + ro + x] = o[i];
@@ -425,7 +480,7 @@ __device__ __forceinline__ Nb3 plane_nbs(const VDom &d, int z) {
 // One strip of tiles: column block starting at xs, plane z, rows [y0, y1).
 // VEC (D2Q9, CPT = 4): the contiguous 4-cells-per-thread compute above.
 // Thread 0 refills a stage after a CTA barrier says every thread is done with it.
-template <int Q, int NT, int CPT, bool VEC = false>
+template <int Q, int NT, int CPT, bool VEC = false, bool PL = false>
 __device__ __forceinline__ void ring_strip(const VDom &d, const float *__restrict__ fin,
                                            float *__restrict__ fout, int xs, int z, int y0, int y1,
                                            int stages, unsigned char *smem) {
@@ -467,12 +522,11 @@ __device__ __forceinline__ void ring_strip(const VDom &d, const float *__restric
         j0 = j1;
         const int y = y0 + k;
         const Nb3 Y = nb3<true>(y, d.ny, d.wall_y);
-        const long long ro = row_offset(d, y, z);
         // (D3Q19 keeps one body: a second copy of its larger tile code measured slower)
-        if (Q == 19 || zedge || Y.wall[0] || Y.wall[2])
-            ring_tile<Q, NT, CPT, VEC, true>(d, sb, ey_slot, Y, Z, fout, ro, xs, tid, [] {});
+        if (Q == 19 || zedge || Y.wall[0] || Y.wall[2] || (PL && (y <= 1 || y >= d.ny - 2)))
+            ring_tile<Q, NT, CPT, VEC, true, PL>(d, sb, ey_slot, Y, Z, fout, y, z, xs, tid, [] {});
         else
-            ring_tile<Q, NT, CPT, VEC, false>(d, sb, ey_slot, Y, Z, fout, ro, xs, tid, [] {});
+            ring_tile<Q, NT, CPT, VEC, false, PL>(d, sb, ey_slot, Y, Z, fout, y, z, xs, tid, [] {});
         __syncthreads();
         if (tid == 0 && k + stages < n) {
             fence_proxy_async_smem();
@@ -502,7 +556,7 @@ __device__ __forceinline__ void ring_strip(const VDom &d, const float *__restric
 // others.  Stage reuse is the same as above: tile k+stages (and the eps ring
 // slot it loads, last read by tile k) is issued after every warp is done with
 // tile k.  stages <= kBarBytes / 16.
-template <int Q, int NT, int CPT, bool VEC = false>
+template <int Q, int NT, int CPT, bool VEC = false, bool PL = false>
 __device__ __forceinline__ void ring_strip_ws(const VDom &d, const float *__restrict__ fin,
                                               float *__restrict__ fout, int xs, int z, int y0, int y1,
                                               int stages, unsigned char *smem) {
@@ -569,21 +623,20 @@ __device__ __forceinline__ void ring_strip_ws(const VDom &d, const float *__rest
         j0 = j1;
         const int y = y0 + k;
         const Nb3 Y = nb3<true>(y, d.ny, d.wall_y);
-        const long long ro = row_offset(d, y, z);
         uint64_t *const emp = &empty[s];
         auto release = [&] {
             __syncwarp();       // every lane's reads of the stage precede the arrive
             if (lane == 0) mbar_arrive(emp);
         };
-        if (Q == 19 || zedge || Y.wall[0] || Y.wall[2])
-            ring_tile<Q, NT, CPT, VEC, true>(d, sb, ey_slot, Y, Z, fout, ro, xs, tid, release);
+        if (Q == 19 || zedge || Y.wall[0] || Y.wall[2] || (PL && (y <= 1 || y >= d.ny - 2)))
+            ring_tile<Q, NT, CPT, VEC, true, PL>(d, sb, ey_slot, Y, Z, fout, y, z, xs, tid, release);
         else
-            ring_tile<Q, NT, CPT, VEC, false>(d, sb, ey_slot, Y, Z, fout, ro, xs, tid, release);
+            ring_tile<Q, NT, CPT, VEC, false, PL>(d, sb, ey_slot, Y, Z, fout, y, z, xs, tid, release);
         if (++s == stages) { s = 0; par ^= 1u; }
     }
 }
 
-template <int Q, int NT, int CPT, bool VEC = false, bool WS = false>
+template <int Q, int NT, int CPT, bool VEC = false, bool WS = false, bool PL = false>
 __global__ void __launch_bounds__(WS ? NT + 32 : NT) k_step_tma_ring(const VDom d,
                                                                       const float *__restrict__ fin,
                                                                       float *__restrict__ fout,
@@ -597,9 +650,9 @@ __global__ void __launch_bounds__(WS ? NT + 32 : NT) k_step_tma_ring(const VDom 
     const int y0 = (int)((long long)yc * d.ny / per_y);
     const int y1 = (int)((long long)(yc + 1) * d.ny / per_y);
     if constexpr (WS)
-        ring_strip_ws<Q, NT, CPT, VEC>(d, fin, fout, xt * NT * CPT, z, y0, y1, stages, smem);
+        ring_strip_ws<Q, NT, CPT, VEC, PL>(d, fin, fout, xt * NT * CPT, z, y0, y1, stages, smem);
     else
-        ring_strip<Q, NT, CPT, VEC>(d, fin, fout, xt * NT * CPT, z, y0, y1, stages, smem);
+        ring_strip<Q, NT, CPT, VEC, PL>(d, fin, fout, xt * NT * CPT, z, y0, y1, stages, smem);
 }
 
 // Interleaved persistent step.  CTA b of G takes tiles b, b + G, b + 2G, ...
@@ -660,7 +713,7 @@ struct IlvBatchCursor {        // a batch: tile table {dom, row, x0}, descriptor
     __device__ void next() { t += G; }
 };
 
-template <int Q, int NT, int CPT, bool VEC, class Cur>
+template <int Q, int NT, int CPT, bool VEC, bool PL, class Cur>
 __device__ __forceinline__ void ilv_run(Cur cur, const int *status, int ntiles, int stages,
                                         unsigned char *smem) {
     constexpr int TW = NT * CPT;
@@ -725,28 +778,30 @@ __device__ __forceinline__ void ilv_run(Cur cur, const int *status, int ntiles, 
         row_nbs<Q>(d, cur.row(), y, z, Y, Z);
         const float *sb = buf + s * (NS * SEG);
         const float *ey_slot[3] = {sb + Q * SEG, sb + (Q + NZR) * SEG, sb + (Q + 2 * NZR) * SEG};
-        const long long ro = row_offset(d, y, z);
         uint64_t *const emp = &empty[s];
         auto release = [&] {
             __syncwarp();       // every lane's reads of the stage precede the arrive
             if (lane == 0) mbar_arrive(emp);
         };
         const int xs = cur.xs(TW);
-        if (Q == 19 || Y.wall[0] || Y.wall[2] || Z.wall[0] || Z.wall[2])
-            ring_tile<Q, NT, CPT, VEC, true>(d, sb, ey_slot, Y, Z, cur.fout(), ro, xs, tid, release);
+        if (Q == 19 || Y.wall[0] || Y.wall[2] || Z.wall[0] || Z.wall[2] ||
+            (PL && (y <= 1 || y >= d.ny - 2)))
+            ring_tile<Q, NT, CPT, VEC, true, PL>(d, sb, ey_slot, Y, Z, cur.fout(), y, z, xs, tid,
+                                                 release);
         else
-            ring_tile<Q, NT, CPT, VEC, false>(d, sb, ey_slot, Y, Z, cur.fout(), ro, xs, tid, release);
+            ring_tile<Q, NT, CPT, VEC, false, PL>(d, sb, ey_slot, Y, Z, cur.fout(), y, z, xs, tid,
+                                                  release);
         cur.next();
         if (++s == stages) { s = 0; par ^= 1u; }
     }
 }
 
-template <int Q, int NT, int CPT, bool VEC>
+template <int Q, int NT, int CPT, bool VEC, bool PL = false>
 __global__ void __launch_bounds__(NT + 32) k_step_tma_ilv(const VDom d, const float *__restrict__ fin,
                                                            float *__restrict__ fout, int ntx,
                                                            int ntiles, int stages) {
     extern __shared__ __align__(128) unsigned char smem[];
-    ilv_run<Q, NT, CPT, VEC>(IlvCursor(d, fin, fout, (int)blockIdx.x, (int)gridDim.x, ntx), d.status,
+    ilv_run<Q, NT, CPT, VEC, PL>(IlvCursor(d, fin, fout, (int)blockIdx.x, (int)gridDim.x, ntx), d.status,
                              ntiles, stages, smem);
 }
 
@@ -758,18 +813,18 @@ __global__ void __launch_bounds__(NT + 32) k_step_ilv_batched(const VDom *__rest
                                                                int ntiles, int parity, int stages,
                                                                int *status) {
     extern __shared__ __align__(128) unsigned char smem[];
-    ilv_run<9, NT, CPT, VEC>(IlvBatchCursor(doms, tiles, (int)blockIdx.x, (int)gridDim.x, parity),
+    ilv_run<9, NT, CPT, VEC, false>(IlvBatchCursor(doms, tiles, (int)blockIdx.x, (int)gridDim.x, parity),
                              status, ntiles, stages, smem);
 }
 
-template <int Q, int NT, int CPT, bool VEC>
+template <int Q, int NT, int CPT, bool VEC, bool PL = false>
 static cudaError_t launch_ilv_t(const VDom &d, const float *fin, float *fout, int stages,
                                 cudaStream_t stream) {
     constexpr int TW = NT * CPT;
     constexpr int NS = Q + EpsRows<Q>::N;
     const size_t smem = kBarBytes + (size_t)stages * NS * (TW + 8) * sizeof(float);
     if (stages < 2 || stages > kBarBytes / 16 || smem > 227 * 1024) return cudaErrorInvalidValue;
-    auto kern = k_step_tma_ilv<Q, NT, CPT, VEC>;
+    auto kern = k_step_tma_ilv<Q, NT, CPT, VEC, PL>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, occ = 0;
@@ -823,7 +878,7 @@ static int pick_per_y(int ncol, int ny, long long resident) {
     return best;
 }
 
-template <int Q, int NT, int CPT, bool VEC = false, bool WS = false>
+template <int Q, int NT, int CPT, bool VEC = false, bool WS = false, bool PL = false>
 static cudaError_t launch_ring_t(const VDom &d, const float *fin, float *fout, int stages,
                                  cudaStream_t stream) {
     constexpr int TW = NT * CPT;
@@ -832,7 +887,7 @@ static cudaError_t launch_ring_t(const VDom &d, const float *fin, float *fout, i
         kBarBytes + (size_t)(stages * Q + (stages + 2) * NZR) * (TW + 8) * sizeof(float);
     const int max_stages = WS ? kBarBytes / 16 : kBarBytes / 8;
     if (stages < 2 || stages > max_stages || smem > 227 * 1024) return cudaErrorInvalidValue;
-    auto kern = k_step_tma_ring<Q, NT, CPT, VEC, WS>;
+    auto kern = k_step_tma_ring<Q, NT, CPT, VEC, WS, PL>;
     constexpr int nthreads = WS ? NT + 32 : NT;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -965,8 +1020,42 @@ cudaError_t launch_ring_batched(const VDom *doms, const Tile *strips, int nstrip
 // per tile, L.rows -> pipeline stages; kind 1 the plain pipeline, 2 the
 // porosity ring, 3 the ring with contiguous cells (D2Q9), 4 and 5 the
 // warp-specialised forms of 2 and 3 (one extra producer warp)
+// The launch shapes with a plates-on-nodes instance (wall_kind 1).
+static bool plate_shape(int q, const Launch &L) {
+    const int nt = 32 * L.warps;
+    if (q == 9)
+        return (L.kind == 2 && nt == 128 && (L.cpt == 2 || L.cpt == 4)) ||
+               ((L.kind == 5 || L.kind == 7) && L.cpt == 4 && (nt == 64 || nt == 128));
+    return (L.kind == 2 && nt == 128 && L.cpt == 1) ||
+           ((L.kind == 3 || L.kind == 5 || L.kind == 7) && nt == 128 && L.cpt == 2);
+}
+
+bool launch_has_plates(int q, Launch L) { return L.kind == 0 || plate_shape(q, L); }
+
+static cudaError_t launch_plates(int q, const VDom &d, const float *fin, float *fout, Launch L,
+                                 cudaStream_t stream) {
+    const int nt = 32 * L.warps;
+    const int st = L.rows;
+    if (!plate_shape(q, L)) return cudaErrorInvalidValue;
+    if (q == 9) {
+        if (L.kind == 2)
+            return L.cpt == 2 ? launch_ring_t<9, 128, 2, false, false, true>(d, fin, fout, st, stream)
+                              : launch_ring_t<9, 128, 4, false, false, true>(d, fin, fout, st, stream);
+        if (L.kind == 5)
+            return nt == 64 ? launch_ring_t<9, 64, 4, true, true, true>(d, fin, fout, st, stream)
+                            : launch_ring_t<9, 128, 4, true, true, true>(d, fin, fout, st, stream);
+        return nt == 64 ? launch_ilv_t<9, 64, 4, true, true>(d, fin, fout, st, stream)
+                        : launch_ilv_t<9, 128, 4, true, true>(d, fin, fout, st, stream);
+    }
+    if (L.kind == 2) return launch_ring_t<19, 128, 1, false, false, true>(d, fin, fout, st, stream);
+    if (L.kind == 3) return launch_ring_t<19, 128, 2, true, false, true>(d, fin, fout, st, stream);
+    if (L.kind == 5) return launch_ring_t<19, 128, 2, true, true, true>(d, fin, fout, st, stream);
+    return launch_ilv_t<19, 128, 2, true, true>(d, fin, fout, st, stream);
+}
+
 cudaError_t launch_step_tma(int q, const VDom &d, const float *fin, float *fout, Launch L,
                             cudaStream_t stream) {
+    if (d.nee) return launch_plates(q, d, fin, fout, L, stream);
     const int nt = 32 * L.warps;
     if (L.kind == 6) {                  // interleaved tiles, strided cells per thread
         if (q == 9 && nt == 128 && L.cpt == 2) return launch_ilv_t<9, 128, 2, false>(d, fin, fout, L.rows, stream);

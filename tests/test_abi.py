@@ -126,3 +126,18 @@ def test_oracle_and_cuda_path_share_nothing():
     assert "vans.h" not in ora and "csrc" not in ora
     ora_py = open(os.path.join(ROOT, "oracle", "__init__.py")).read()
     assert "paper_1406_6438_gb300" not in ora_py
+
+
+def test_plates_on_nodes_parameters(lib):
+    """wall_kind 1 (plates on nodes): y walls only, ny >= 3, single domain."""
+    assert lib.vans_state_floats(ctypes.byref(Params(q=9, nx=8, ny=5, wall_mask=2,
+                                                     wall_kind=1).c())) > 0
+    for bad in (dict(wall_mask=0), dict(ny=2), dict(wall_kind=2)):
+        kw = dict(q=9, nx=8, ny=5, wall_mask=2, wall_kind=1)
+        kw.update(bad)
+        assert lib.vans_state_floats(ctypes.byref(Params(**kw).c())) == -1
+    # z walls with plates on nodes, and batches, are refused
+    assert lib.vans_state_floats(ctypes.byref(Params(q=19, nx=8, ny=5, nz=4, wall_mask=6,
+                                                     wall_kind=1).c())) == -1
+    one = (type(Params().c()) * 1)(Params(q=9, nx=8, ny=5, wall_mask=2, wall_kind=1).c())
+    assert lib.vans_batch_workspace_bytes(one, 1) == 0
