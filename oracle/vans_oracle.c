@@ -43,7 +43,7 @@
  *   R7  Walls are half-way bounce-back: a population that would leave through a
  *       wall face returns to its node in the opposite direction after one step.
  *   R8  nu = cs^2 (tau - 1/2) dt, p = cs^2 rho (stated after Eq. VNS2), dt = 1.
- *   R9 wall_kind 1 (the paper's validation runs, Sec. "Examples and
+ *   R9  wall_kind 1 (the paper's validation runs, Sec. "Examples and
  *       discussions", apply the non-equilibrium extrapolation scheme of Guo,
  *       Zheng & Shi 2002 at both plates): the rows y = 0 and y = ny-1 are nodes
  *       on the plates (H = ny - 1).  A plate node x_b takes
