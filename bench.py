@@ -313,6 +313,15 @@ def bench_adjoint(torch, V, W, args=None):
     cells = p["nx"] * p["ny"]
     out = {"workload": "D2Q9 512x512 channel, eps noise [0.4,1.0], tau 0.8, outlet flux gradient",
            "steps": n, "checkpoint_every": every, "unit": "MLUPS (backward pass, wall clock)"}
+    # FP64 central finite differences of the oracle at 32 cells of this workload
+    # (a committed data file written by tests/golden/make_adjoint_fd.py)
+    gold = None
+    gpath = os.path.join(ROOT, "tests", "golden", "adjoint_channel_512_fd.json")
+    if os.path.exists(gpath):
+        with open(gpath) as fh:
+            gold = json.load(fh)
+        if gold.get("nsteps") != n:
+            gold = None
     for bits in (32, 64):
         s = V.Solver(p)
         s.set_eps(torch.from_numpy(eps).cuda().view(-1))
@@ -335,9 +344,14 @@ def bench_adjoint(torch, V, W, args=None):
             out["forward_mlups"] = cells * n / (t1 - t0) / 1e6
             out["backward_launches"] = s.launch_count - c0
         out[f"grad_finite_{bits}"] = bool(torch.isfinite(e.grad).all().item())
+        if gold is not None and gold["x_out"] == p["nx"] - 1:
+            g = e.grad.cpu().numpy().astype(np.float64)
+            fd = np.array(gold["dJdeps_fd"])
+            got = np.array([g[tuple(c)] for c in gold["cells_zyx"]])
+            out[f"fd_err_{bits}"] = float(np.abs(got - fd).max() / np.abs(fd).max())
         s.close()
-    out["note"] = ("value: all-FP32 reverse step (max FD error 2.3e-4 at 32 cells); fp64_arith: "
-                   "per-cell reverse arithmetic in FP64 (6.3e-5)")
+    out["note"] = ("value: all-FP32 reverse step; fp64_arith: per-cell reverse arithmetic in FP64; "
+                   "fd_err_*: max over 32 cells of |dJ/deps - FP64 FD| / max |FD|")
     return out
 
 

@@ -19,10 +19,10 @@ template <> __device__ __forceinline__ double vsqrt<double>(double x) { return s
 
 template <int Q, typename T>
 struct MacroT {
-    T dl, e0, R, inv_e, rho;
+    T dl, e0, R, inv_e, rho, rho3;
     T ge[3], j[3], Pc[3], m[3];
     T alpha, beta, dalpha, dbeta;
-    T a, b, mm, sq, D;
+    T a, b, mm, sq, D, inv_D;
     T u[3], un, V[3];
 };
 
@@ -39,7 +39,7 @@ __device__ __forceinline__ void macro_t(const VDom &d, const float h[Q], float e
     M.e0 = e0;
     M.R = e0 + dl;
     M.inv_e = T(1) / e0;
-    M.rho = M.R / e0;
+    M.rho = M.R * M.inv_e;
 #pragma unroll
     for (int c = 0; c < D; ++c) { M.ge[c] = 0; M.j[c] = 0; }
 #pragma unroll
@@ -57,9 +57,9 @@ __device__ __forceinline__ void macro_t(const VDom &d, const float h[Q], float e
     const T ca = (T)d.ca, cb = (T)d.cb;
     if (d.k_mode == 0) {
         const T om = T(1) - e0;
-        a = ca * om * om / e0;
+        a = ca * om * om * M.inv_e;
         b = cb * om;
-        da = -ca * om * (T(1) + e0) / (e0 * e0);
+        da = -ca * om * (T(1) + e0) * (M.inv_e * M.inv_e);
         db = -cb;
     } else if (d.k_mode == 1) {
         a = ca * e0 * e0;
@@ -77,6 +77,7 @@ __device__ __forceinline__ void macro_t(const VDom &d, const float h[Q], float e
     if (d.drag_mode == 1) { b = db = 0; }
     M.alpha = a; M.beta = b; M.dalpha = da; M.dbeta = db;
     const T pc = M.rho / T(3);
+    M.rho3 = pc;
     T mm2 = 0;
 #pragma unroll
     for (int c = 0; c < D; ++c) {
@@ -89,7 +90,8 @@ __device__ __forceinline__ void macro_t(const VDom &d, const float h[Q], float e
     M.mm = vsqrt<T>(mm2);
     M.sq = vsqrt<T>(M.a * M.a + T(4) * M.b * M.mm);
     M.D = M.a + M.sq;
-    const T s = T(2) / M.D;
+    M.inv_D = T(1) / M.D;
+    const T s = T(2) * M.inv_D;
     M.un = M.mm * s;
     const T kd = M.alpha + M.beta * M.un;
 #pragma unroll
@@ -120,6 +122,8 @@ __device__ __forceinline__ void macro_vjp_t(const VDom &d, const MacroT<Q, T> &M
     T betabar = -M.un * Fu;
     const T kd = M.alpha + M.beta * M.un;
     const T ib = (M.un > T(0)) ? M.beta * Fu / M.un : T(0);
+    // reciprocals formed once (each a correctly rounded division); the
+    // quotients below are products with them
     T ubu = 0;
 #pragma unroll
     for (int c = 0; c < D; ++c) {
@@ -127,12 +131,13 @@ __device__ __forceinline__ void macro_vjp_t(const VDom &d, const MacroT<Q, T> &M
         ubu += ubar[c] * M.u[c];
     }
     // u = 2 m / D,  D = a + sqrt(a^2 + 4 b |m|)
-    const T Dbar = -ubu / M.D;
-    const T abar = Dbar * (T(1) + M.a / M.sq);
-    const T bbar = Dbar * T(2) * M.mm / M.sq;
-    const T mmbar = Dbar * T(2) * M.b / M.sq;
+    const T inv_sq = T(1) / M.sq;
+    const T Dbar = -ubu * M.inv_D;
+    const T abar = Dbar * (T(1) + M.a * inv_sq);
+    const T bbar = Dbar * T(2) * M.mm * inv_sq;
+    const T mmbar = Dbar * T(2) * M.b * inv_sq;
     const T im = (M.mm > T(0)) ? mmbar / M.mm : T(0);
-    const T s2 = T(2) / M.D;
+    const T s2 = T(2) * M.inv_D;
 #pragma unroll
     for (int c = 0; c < D; ++c) mbar[c] = ubar[c] * s2 + im * M.m[c];
     // a = R + alpha/2, b = beta/2
@@ -140,18 +145,19 @@ __device__ __forceinline__ void macro_vjp_t(const VDom &d, const MacroT<Q, T> &M
     alphabar += T(0.5) * abar;
     betabar += T(0.5) * bbar;
     // m = j + Pc/2 + R g/2;  Pc = rho grad eps / 3
-    T rhobar = 0;
+    T pg = 0;
 #pragma unroll
     for (int c = 0; c < D; ++c) {
         jbar[c] = mbar[c];
         Pcbar[c] += T(0.5) * mbar[c];
         Rbar += T(0.5) * mbar[c] * (T)d.g[c];
-        rhobar += Pcbar[c] * M.ge[c] / T(3);
-        gbar[c] = M.rho * Pcbar[c] / T(3);
+        pg += Pcbar[c] * M.ge[c];
+        gbar[c] = M.rho3 * Pcbar[c];
     }
+    const T rhobar = pg / T(3);
     // rho = R / eps
-    Rbar += rhobar / M.e0;
-    ebar = -rhobar * M.R / (M.e0 * M.e0);
+    Rbar += rhobar * M.inv_e;
+    ebar = -rhobar * M.rho * M.inv_e;
     ebar += alphabar * M.dalpha + betabar * M.dbeta;
     lam0 = Rbar;
 }
