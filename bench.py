@@ -49,7 +49,7 @@ TRAFFIC = {
     (4, 4, 4, 7, "ee9f0a8d9ac48724"): (679592960 + 559588352 + 680115456 + 557359104) // 2,
     (4, 4, 4, 5, "ee9f0a8d9ac48724"): (681760256 + 559564544 + 681480960 + 556161536) // 2,
 }
-_PIPELINE_SOURCES = ("vans_step_tma.cu", "vans_device.cuh", "vans_tma.cuh")
+_PIPELINE_SOURCES = ("vans_step_tma.cu", "vans_pipeline.cuh", "vans_device.cuh", "vans_tma.cuh")
 KERNEL_SOURCES = {0: ("vans_step.cu", "vans_device.cuh")}
 KERNEL_SOURCES.update({k: _PIPELINE_SOURCES for k in range(1, 8)})
 

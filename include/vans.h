@@ -240,9 +240,12 @@ int vans_step_adjoint(vans_t h, const float *state_t, const float *lam_in, float
 int vans_adjoint_segment(vans_t h, const float *ckpt, float *seg, int len, float *lam, float *tmp,
                          float *grad_acc);
 
-/* Launch shape of the reverse step: cpt cells per lane (1, or 2 for D2Q9),
- * `warps` x `rows` threads per block (at most 8 warps), kind 0.  VANS_ERR_ARG
- * otherwise. */
+/* Launch shape of the reverse step.  kind 0: register-load kernel, cpt cells
+ * per lane (1, or 2 for D2Q9), `warps` x `rows` threads per block (at most 8
+ * warps).  kind 1 (the default, cpt 1, 4 warps, 4 stages): bulk-copy pipeline
+ * with a producer warp, persistent CTAs over the row tiles; `warps` compute
+ * warps (D2Q9: 2 with cpt 1, or 4 with cpt 1 or 2; D3Q19: 4 with cpt 1),
+ * `rows` = pipeline stages (2..8).  VANS_ERR_ARG otherwise. */
 int vans_set_adjoint_launch(vans_t h, const vans_launch *cfg);
 
 /* Arithmetic of the per-cell reverse step: 32 (FP32, the default) or 64 (FP64;

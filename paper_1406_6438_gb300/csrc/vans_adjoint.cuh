@@ -13,6 +13,26 @@
 
 namespace vans {
 
+// Compensated (Neumaier) FP32 accumulation: *s holds the running sum and *c the
+// rounding error lost so far; s + c is the sum to about one FP32 ulp however
+// many steps are added.  The eps gradient is a small residual of large
+// grad-eps sensitivities (they cancel through the transposed stencil), so the
+// plain FP32 running sum would lose most of it over thousands of steps.
+__device__ __forceinline__ void acc2(float *s, float *c, float x) {
+    const float a = *s;
+    const float t = a + x;
+    const float e = (fabsf(a) >= fabsf(x)) ? (a - t) + x : (x - t) + a;
+    *s = t;
+    *c += e;
+}
+
+// the same on values held in registers
+__device__ __forceinline__ void acc2_reg(float &s, float &c, float x) {
+    const float t = s + x;
+    c += (fabsf(s) >= fabsf(x)) ? (s - t) + x : (x - t) + s;
+    s = t;
+}
+
 template <typename T> __device__ __forceinline__ T vsqrt(T x);
 template <> __device__ __forceinline__ float vsqrt<float>(float x) { return sqrtf(x); }
 template <> __device__ __forceinline__ double vsqrt<double>(double x) { return sqrt(x); }

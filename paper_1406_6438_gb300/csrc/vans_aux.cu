@@ -241,18 +241,6 @@ __global__ void k_check(const VDom d, const float *__restrict__ st, int *flag) {
 }
 
 // ------------------------------------------------------ reverse mode -----
-// Compensated (Neumaier) FP32 accumulation: *s holds the running sum and *c the
-// rounding error lost so far; s + c is the sum to about one FP32 ulp however
-// many steps are added.  The eps gradient is a small residual of large
-// grad-eps sensitivities (they cancel through the transposed stencil), so the
-// plain FP32 running sum would lose most of it over thousands of steps.
-__device__ __forceinline__ void acc2(float *s, float *c, float x) {
-    const float a = *s;
-    const float t = a + x;
-    const float e = (fabsf(a) >= fabsf(x)) ? (a - t) + x : (x - t) + a;
-    *s = t;
-    *c += e;
-}
 
 // J = sum over the plane x = x_out of eps rho u_x; one block, fixed-order sum.
 template <int Q>
@@ -586,9 +574,12 @@ static cudaError_t launch_adj_t(const VDom &d, const float *state, const float *
     return cudaGetLastError();
 }
 
-// L.cpt: cells per lane (1 or 2; D3Q19 takes 1), L.warps x L.rows threads per block
+// kind 0: the register-load kernel, L.cpt cells per lane (1 or 2; D3Q19 takes 1),
+// L.warps x L.rows threads per block; kind 1: the bulk-copy pipeline kernel
 cudaError_t launch_step_adjoint(int q, const VDom &d, const float *state, const float *lam_in,
                                 float *lam_out, float *grad, int fp64, Launch L, cudaStream_t s) {
+    if (L.kind == 1) return launch_adjoint_tma(q, d, state, lam_in, lam_out, grad, fp64, L, s);
+    if (L.kind != 0) return cudaErrorInvalidValue;
     if (L.warps < 1 || L.rows < 1 || L.warps * L.rows > 8) return cudaErrorInvalidValue;
     if (q == 9 && L.cpt == 2)
         return fp64 ? launch_adj_t<9, 2, double>(d, state, lam_in, lam_out, grad, L, s)

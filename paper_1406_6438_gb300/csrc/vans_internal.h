@@ -59,6 +59,9 @@ cudaError_t launch_step_monitor(int q, const VDom &d, const float *fin, float *f
                                 float *u, float *stats, cudaStream_t stream);
 cudaError_t launch_step_tma(int q, const VDom &d, const float *fin, float *fout, Launch L,
                             cudaStream_t stream);
+// the reverse step with a bulk-copy pipeline (adjoint launch kind 1)
+cudaError_t launch_adjoint_tma(int q, const VDom &d, const float *state, const float *lam_in,
+                               float *lam_out, float *grad, int fp64, Launch L, cudaStream_t s);
 // whether launch L has an instance for plates on nodes (wall_kind 1)
 bool launch_has_plates(int q, Launch L);
 // kinds 2, 4, 5: strip table (one CTA per strip); 6, 7: interleaved tile table

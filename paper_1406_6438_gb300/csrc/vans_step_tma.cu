@@ -12,74 +12,10 @@
 // unit-stride across a warp (no bank conflicts) and the +-1 column shift of the
 // pull is just an offset.  Stores go straight to global memory, 128 bytes per
 // warp instruction.
-#include "vans_device.cuh"
-#include "vans_tma.cuh"
+#include "vans_pipeline.cuh"
 
 namespace vans {
 
-template <int Q> struct EpsRows;
-template <> struct EpsRows<9> { static constexpr int N = 3; };    // dy = -1, 0, 1
-template <> struct EpsRows<19> { static constexpr int N = 9; };   // (dy, dz) in {-1,0,1}^2
-
-// Stage slot of the porosity row (y + dy, z + dz): D2Q9 dy + 1; D3Q19 the
-// three z-rows of one dy side by side, (dy + 1) * 3 + dz + 1 (the layout of
-// the ring slots, so the same tile compute reads both)
-template <int Q>
-__host__ __device__ constexpr int eps_slot(int dy, int dz) {
-    return Q == 9 ? dy + 1 : (dy + 1) * 3 + (dz + 1);
-}
-
-template <int Q>
-__device__ __forceinline__ void row_nbs(const VDom &d, int row, int &y, int &z, Nb3 &Y, Nb3 &Z) {
-    y = row % d.ny;
-    z = row / d.ny;
-    Y = nb3<true>(y, d.ny, d.wall_y);
-    if (Q == 19) {
-        Z = nb3<true>(z, d.nz, d.wall_z);
-    } else {
-        Z.r[0] = Z.r[1] = Z.r[2] = 0;
-        Z.wall[0] = Z.wall[1] = Z.wall[2] = false;
-    }
-}
-
-constexpr int kBarBytes = 128;   // room for up to 16 mbarriers in front of the stages
-
-// Issue the bulk copies of the tile (row, xs) into stage buffer sb (one thread).
-template <int Q, int TW>
-__device__ __forceinline__ void issue_tile(const VDom &d, const float *__restrict__ fin, int row,
-                                           int xs, float *sb, uint64_t *bar) {
-    using L = Lat<Q>;
-    constexpr int SEG = TW + 8;
-    constexpr int NS = Q + EpsRows<Q>::N;
-    int y, z;
-    Nb3 Y, Z;
-    row_nbs<Q>(d, row, y, z, Y, Z);
-    const int nval = min(TW, d.nx - xs);
-    // columns xs-4 .. xs+round4(nval)+3: the cells, the +-1 neighbours (halo
-    // columns included) and 16-byte alignment on both ends
-    const uint32_t bytes = (uint32_t)((((nval + 3) & ~3) + 8) * 4);
-    mbar_arrive_expect_tx(bar, bytes * NS);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const int ey = L::ey(i), ez = L::ez(i);
-        const bool bb = Y.wall[1 - ey] || Z.wall[1 - ez];
-        const int si = bb ? L::opp(i) : i;
-        const long long ro = bb ? row_offset(d, y, z) : row_offset(d, Y.r[1 - ey], Z.r[1 - ez]);
-        bulk_g2s(sb + i * SEG, fin + si * d.plane + ro + xs - 4, bytes, bar);
-    }
-    // the porosity rows are read again by the tiles of the neighbouring rows:
-    // keep them in L2 longest
-    const uint64_t again = l2_evict_last();
-#pragma unroll
-    for (int dz = -1; dz <= 1; ++dz)
-#pragma unroll
-        for (int dy = -1; dy <= 1; ++dy) {
-            if (Q == 9 && dz != 0) continue;
-            const float *src = d.eps + row_offset(d, Y.r[1 + dy], Z.r[1 + dz]) + xs - 4;
-            bulk_g2s_hint(sb + (Q + eps_slot<Q>(dy, dz)) * SEG, src, bytes, bar, again);
-        }
-    (void)NS;
-}
 
 template <int Q, int NT, int CPT>
 __global__ void __launch_bounds__(NT) k_step_tma(const VDom d, const float *__restrict__ fin,

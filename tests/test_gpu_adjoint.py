@@ -5,16 +5,19 @@ import pytest
 
 import oracle as O
 from paper_1406_6438_gb300 import workloads as W
+from paper_1406_6438_gb300._binding import Launch
 from tests._gpu import solver, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
 
-def _gpu_grad(p, eps, nsteps, every, x_out, bits=32):
+def _gpu_grad(p, eps, nsteps, every, x_out, bits=32, adj_launch=None):
     torch = torch_cuda()
     from paper_1406_6438_gb300.adjoint import outlet_flux
     s = solver(p, eps)
     s.set_adjoint_precision(bits)
+    if adj_launch is not None:
+        s.set_adjoint_launch(adj_launch)
     e = torch.from_numpy(np.ascontiguousarray(eps)).cuda().requires_grad_(True)
     J = outlet_flux(e, s, nsteps, every, x_out)
     J.backward()
@@ -38,20 +41,37 @@ ADJ_CASES = [
 ]
 
 
+@pytest.mark.parametrize("adj_launch", [None, Launch(1, 4, 4, 1)])
 @pytest.mark.parametrize("bits", [32, 64])
 @pytest.mark.parametrize("p,nsteps,every", ADJ_CASES)
-def test_adjoint_matches_oracle_discrete_adjoint(p, nsteps, every, bits):
+def test_adjoint_matches_oracle_discrete_adjoint(p, nsteps, every, bits, adj_launch):
     """dJ/deps of every cell from the GPU adjoint (FP32 states and compensated
-    FP32 accumulation; per-cell arithmetic in FP32 or FP64) within 1e-4 of the
-    oracle's FP64 adjoint, relative to max |dJ/deps|."""
+    FP32 accumulation; per-cell arithmetic in FP32 or FP64; the register-load
+    reverse step or the bulk-copy pipelined one) within 1e-4 of the oracle's
+    FP64 adjoint, relative to max |dJ/deps|."""
     shape = (p["nz"], p["ny"], p["nx"])
     eps = W.smoothed_noise(shape, 4.0, 0.4, 1.0, seed=shape[1] + nsteps)
     x_out = p["nx"] - 1
     J_o, g_o = O.adjoint(O.Params(**p), eps.astype(np.float64), nsteps, x_out)
-    J, g = _gpu_grad(p, eps, nsteps, every, x_out, bits)
+    J, g = _gpu_grad(p, eps, nsteps, every, x_out, bits, adj_launch)
     assert abs(J - J_o) <= 1e-5 * abs(J_o)
     err = np.abs(g - g_o).max() / np.abs(g_o).max()
     assert err <= 1e-4, err
+
+
+@pytest.mark.parametrize("AL", [Launch(1, 4, 4, 1), Launch(2, 4, 3, 1), Launch(1, 2, 5, 1),
+                                Launch(1, 4, 2, 1)])
+def test_pipelined_reverse_step_equals_register_load_kernel(AL):
+    """The two reverse-step kernels run the same per-cell arithmetic and the
+    same accumulation order: gradients agree to FP32 rounding (the compiler may
+    contract a multiply-add differently in the two instantiations)."""
+    p = W.params(q=9, nx=150, ny=37, wall_mask=2, tau=0.75, g=(4e-5, 0, 0), drag_mode=2,
+                 k_mode=0, d_p=8.0, u_wall=(0.005, 0.0, 0.0))
+    eps = W.smoothed_noise((1, 37, 150), 4.0, 0.4, 1.0, seed=12)
+    J0, g0 = _gpu_grad(p, eps, 80, 20, 149)
+    J1, g1 = _gpu_grad(p, eps, 80, 20, 149, adj_launch=AL)
+    assert J0 == J1
+    assert np.abs(g1 - g0).max() <= 1e-5 * np.abs(g0).max()
 
 
 def _pop_of(s, state):
