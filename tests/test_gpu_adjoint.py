@@ -41,7 +41,7 @@ ADJ_CASES = [
 ]
 
 
-@pytest.mark.parametrize("adj_launch", [None, Launch(1, 4, 4, 1)])
+@pytest.mark.parametrize("adj_launch", [Launch(1, 4, 2, 0), Launch(1, 4, 4, 1)])
 @pytest.mark.parametrize("bits", [32, 64])
 @pytest.mark.parametrize("p,nsteps,every", ADJ_CASES)
 def test_adjoint_matches_oracle_discrete_adjoint(p, nsteps, every, bits, adj_launch):
@@ -68,7 +68,7 @@ def test_pipelined_reverse_step_equals_register_load_kernel(AL):
     p = W.params(q=9, nx=150, ny=37, wall_mask=2, tau=0.75, g=(4e-5, 0, 0), drag_mode=2,
                  k_mode=0, d_p=8.0, u_wall=(0.005, 0.0, 0.0))
     eps = W.smoothed_noise((1, 37, 150), 4.0, 0.4, 1.0, seed=12)
-    J0, g0 = _gpu_grad(p, eps, 80, 20, 149)
+    J0, g0 = _gpu_grad(p, eps, 80, 20, 149, adj_launch=Launch(1, 4, 2, 0))
     J1, g1 = _gpu_grad(p, eps, 80, 20, 149, adj_launch=AL)
     assert J0 == J1
     assert np.abs(g1 - g0).max() <= 1e-5 * np.abs(g0).max()
