@@ -22,9 +22,9 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "adjoint_channel_512_
 def test_adjoint_gradient_matches_fp64_finite_differences_at_32_cells(bits, tol):
     """bits = 64: per-cell reverse arithmetic in FP64 (FP32 states, lambda and
     compensated FP32 accumulation): within 1e-4 of the FD values, relative to
-    their maximum (measured 6.3e-5).  bits = 32: all-FP32 reverse step; the eps
+    their maximum (measured 5.0e-5).  bits = 32: all-FP32 reverse step; the eps
     gradient is a ~700x smaller residual of the grad-eps sensitivities, so FP32
-    per-cell rounding leaves 2.3e-4 (median 2e-5) at the worst of the 32 cells."""
+    per-cell rounding leaves 1.8e-4 at the worst of the 32 cells."""
     torch = torch_cuda()
     from paper_1406_6438_gb300.adjoint import outlet_flux
     gold = json.load(open(GOLDEN))
