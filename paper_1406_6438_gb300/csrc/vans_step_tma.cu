@@ -178,7 +178,7 @@ __device__ __forceinline__ void issue_tile_ring(const VDom &d, const float *__re
 // comes in one or two aligned V-wide shared loads (8 or 16 bytes) and each
 // output row leaves in one V-wide global store.  Segment position p holds
 // column xs - 4 + p.
-template <int Q, int NT, int V, bool EDGE, bool PL, class Rel>
+template <int Q, int NT, int V, bool EDGE, bool PL, bool RAG, class Rel>
 __device__ __forceinline__ void ring_tile_vec(const VDom &d, const float *__restrict__ sb,
                                               const float *const ey_slot[3], const Nb3 &Y,
                                               const Nb3 &Z, float *__restrict__ fout, int y, int z,
@@ -197,6 +197,12 @@ __device__ __forceinline__ void ring_tile_vec(const VDom &d, const float *__rest
     const bool plo = nee && y == 1, phi = nee && y == d.ny - 2;
     const long long ro = row_offset(d, y, z);
     const int x0l = V * tid;
+    // RAG (batched instances): a warp whose cells all lie past the last column
+    // (the ragged last tile of a row) has nothing to compute or store
+    if (RAG && xs + V * (tid & ~31) >= d.nx) {
+        release();
+        return;
+    }
     auto ywall = [&](int k) { return EDGE && Y.wall[k]; };
     auto zwall = [&](int k) { return EDGE && Z.wall[k]; };
     auto vload = [&](const float *row, int p, float out[V]) {
@@ -313,8 +319,10 @@ __device__ __forceinline__ void ring_tile_vec(const VDom &d, const float *__rest
 // EDGE = false: the tile's row touches no wall (the wall flags are known to be
 // false at compile time, which drops the per-direction selects).  PL: the
 // instance handles plates on nodes (wall_kind 1); the others carry none of that
-// code (it would raise their register count).
-template <int Q, int NT, int CPT, bool VEC, bool EDGE, bool PL, class Rel>
+// code (it would raise their register count).  RAG (the batched instances,
+// whose domains end in ragged tiles): warps past the row's last column skip the
+// tile; the single-domain instances measured slower with the test in place.
+template <int Q, int NT, int CPT, bool VEC, bool EDGE, bool PL, bool RAG, class Rel>
 __device__ __forceinline__ void ring_tile(const VDom &d, const float *__restrict__ sb,
                                           const float *const ey_slot[3], const Nb3 &Y, const Nb3 &Z,
                                           float *__restrict__ fout, int y, int z, int xs, int tid,
@@ -322,7 +330,7 @@ __device__ __forceinline__ void ring_tile(const VDom &d, const float *__restrict
     using L = Lat<Q>;
     constexpr int SEG = NT * CPT + 8;
     if constexpr (VEC) {
-        ring_tile_vec<Q, NT, CPT, EDGE, PL>(d, sb, ey_slot, Y, Z, fout, y, z, xs, tid, release);
+        ring_tile_vec<Q, NT, CPT, EDGE, PL, RAG>(d, sb, ey_slot, Y, Z, fout, y, z, xs, tid, release);
     } else {
         // plates on nodes (PL instances only): a plate row is written by its
         // fluid neighbour row
@@ -358,6 +366,7 @@ __device__ __forceinline__ void ring_tile(const VDom &d, const float *__restrict
 #pragma unroll
         for (int cc = 0; cc < CPT; ++cc) {
             const int x = xs + tid + cc * NT;
+            if (RAG && xs + (tid & ~31) + cc * NT >= d.nx) continue;   // whole warp past nx
             float o[Q];
             if (EDGE) apply_moving_wall<Q>(d, Y.wall[2], Z, et[cc][0], h[cc]);
             Macro<Q> M;
@@ -416,7 +425,7 @@ __device__ __forceinline__ Nb3 plane_nbs(const VDom &d, int z) {
 // One strip of tiles: column block starting at xs, plane z, rows [y0, y1).
 // VEC (D2Q9, CPT = 4): the contiguous 4-cells-per-thread compute above.
 // Thread 0 refills a stage after a CTA barrier says every thread is done with it.
-template <int Q, int NT, int CPT, bool VEC = false, bool PL = false>
+template <int Q, int NT, int CPT, bool VEC = false, bool PL = false, bool RAG = false>
 __device__ __forceinline__ void ring_strip(const VDom &d, const float *__restrict__ fin,
                                            float *__restrict__ fout, int xs, int z, int y0, int y1,
                                            int stages, unsigned char *smem) {
@@ -460,9 +469,11 @@ __device__ __forceinline__ void ring_strip(const VDom &d, const float *__restric
         const Nb3 Y = nb3<true>(y, d.ny, d.wall_y);
         // (D3Q19 keeps one body: a second copy of its larger tile code measured slower)
         if (Q == 19 || zedge || Y.wall[0] || Y.wall[2] || (PL && (y <= 1 || y >= d.ny - 2)))
-            ring_tile<Q, NT, CPT, VEC, true, PL>(d, sb, ey_slot, Y, Z, fout, y, z, xs, tid, [] {});
+            ring_tile<Q, NT, CPT, VEC, true, PL, RAG>(d, sb, ey_slot, Y, Z, fout, y, z, xs, tid,
+                                                      [] {});
         else
-            ring_tile<Q, NT, CPT, VEC, false, PL>(d, sb, ey_slot, Y, Z, fout, y, z, xs, tid, [] {});
+            ring_tile<Q, NT, CPT, VEC, false, PL, RAG>(d, sb, ey_slot, Y, Z, fout, y, z, xs, tid,
+                                                       [] {});
         __syncthreads();
         if (tid == 0 && k + stages < n) {
             fence_proxy_async_smem();
@@ -492,7 +503,7 @@ __device__ __forceinline__ void ring_strip(const VDom &d, const float *__restric
 // others.  Stage reuse is the same as above: tile k+stages (and the eps ring
 // slot it loads, last read by tile k) is issued after every warp is done with
 // tile k.  stages <= kBarBytes / 16.
-template <int Q, int NT, int CPT, bool VEC = false, bool PL = false>
+template <int Q, int NT, int CPT, bool VEC = false, bool PL = false, bool RAG = false>
 __device__ __forceinline__ void ring_strip_ws(const VDom &d, const float *__restrict__ fin,
                                               float *__restrict__ fout, int xs, int z, int y0, int y1,
                                               int stages, unsigned char *smem) {
@@ -565,9 +576,11 @@ __device__ __forceinline__ void ring_strip_ws(const VDom &d, const float *__rest
             if (lane == 0) mbar_arrive(emp);
         };
         if (Q == 19 || zedge || Y.wall[0] || Y.wall[2] || (PL && (y <= 1 || y >= d.ny - 2)))
-            ring_tile<Q, NT, CPT, VEC, true, PL>(d, sb, ey_slot, Y, Z, fout, y, z, xs, tid, release);
+            ring_tile<Q, NT, CPT, VEC, true, PL, RAG>(d, sb, ey_slot, Y, Z, fout, y, z, xs, tid,
+                                                      release);
         else
-            ring_tile<Q, NT, CPT, VEC, false, PL>(d, sb, ey_slot, Y, Z, fout, y, z, xs, tid, release);
+            ring_tile<Q, NT, CPT, VEC, false, PL, RAG>(d, sb, ey_slot, Y, Z, fout, y, z, xs, tid,
+                                                       release);
         if (++s == stages) { s = 0; par ^= 1u; }
     }
 }
@@ -649,7 +662,7 @@ struct IlvBatchCursor {        // a batch: tile table {dom, row, x0}, descriptor
     __device__ void next() { t += G; }
 };
 
-template <int Q, int NT, int CPT, bool VEC, bool PL, class Cur>
+template <int Q, int NT, int CPT, bool VEC, bool PL, bool RAG, class Cur>
 __device__ __forceinline__ void ilv_run(Cur cur, const int *status, int ntiles, int stages,
                                         unsigned char *smem) {
     constexpr int TW = NT * CPT;
@@ -722,11 +735,11 @@ __device__ __forceinline__ void ilv_run(Cur cur, const int *status, int ntiles, 
         const int xs = cur.xs(TW);
         if (Q == 19 || Y.wall[0] || Y.wall[2] || Z.wall[0] || Z.wall[2] ||
             (PL && (y <= 1 || y >= d.ny - 2)))
-            ring_tile<Q, NT, CPT, VEC, true, PL>(d, sb, ey_slot, Y, Z, cur.fout(), y, z, xs, tid,
-                                                 release);
+            ring_tile<Q, NT, CPT, VEC, true, PL, RAG>(d, sb, ey_slot, Y, Z, cur.fout(), y, z, xs,
+                                                      tid, release);
         else
-            ring_tile<Q, NT, CPT, VEC, false, PL>(d, sb, ey_slot, Y, Z, cur.fout(), y, z, xs, tid,
-                                                  release);
+            ring_tile<Q, NT, CPT, VEC, false, PL, RAG>(d, sb, ey_slot, Y, Z, cur.fout(), y, z, xs,
+                                                       tid, release);
         cur.next();
         if (++s == stages) { s = 0; par ^= 1u; }
     }
@@ -737,8 +750,8 @@ __global__ void __launch_bounds__(NT + 32) k_step_tma_ilv(const VDom d, const fl
                                                            float *__restrict__ fout, int ntx,
                                                            int ntiles, int stages) {
     extern __shared__ __align__(128) unsigned char smem[];
-    ilv_run<Q, NT, CPT, VEC, PL>(IlvCursor(d, fin, fout, (int)blockIdx.x, (int)gridDim.x, ntx), d.status,
-                             ntiles, stages, smem);
+    ilv_run<Q, NT, CPT, VEC, PL, false>(
+        IlvCursor(d, fin, fout, (int)blockIdx.x, (int)gridDim.x, ntx), d.status, ntiles, stages, smem);
 }
 
 // Batched D2Q9, interleaved: the tile table lists every (domain, row, column
@@ -749,8 +762,9 @@ __global__ void __launch_bounds__(NT + 32) k_step_ilv_batched(const VDom *__rest
                                                                int ntiles, int parity, int stages,
                                                                int *status) {
     extern __shared__ __align__(128) unsigned char smem[];
-    ilv_run<9, NT, CPT, VEC, false>(IlvBatchCursor(doms, tiles, (int)blockIdx.x, (int)gridDim.x, parity),
-                             status, ntiles, stages, smem);
+    ilv_run<9, NT, CPT, VEC, false, true>(
+        IlvBatchCursor(doms, tiles, (int)blockIdx.x, (int)gridDim.x, parity), status, ntiles,
+        stages, smem);
 }
 
 template <int Q, int NT, int CPT, bool VEC, bool PL = false>
@@ -790,9 +804,9 @@ __global__ void __launch_bounds__(WS ? NT + 32 : NT) k_step_ring_batched(
     const float *fin = parity ? d.f[1] : d.f[0];
     float *fout = parity ? d.f[0] : d.f[1];
     if constexpr (WS)
-        ring_strip_ws<9, NT, CPT, VEC>(d, fin, fout, S.x0, 0, S.row, S.pad, stages, smem);
+        ring_strip_ws<9, NT, CPT, VEC, false, true>(d, fin, fout, S.x0, 0, S.row, S.pad, stages, smem);
     else
-        ring_strip<9, NT, CPT, VEC>(d, fin, fout, S.x0, 0, S.row, S.pad, stages, smem);
+        ring_strip<9, NT, CPT, VEC, false, true>(d, fin, fout, S.x0, 0, S.row, S.pad, stages, smem);
 }
 
 // Strips per (column block, plane): the smallest count whose grid fills the
