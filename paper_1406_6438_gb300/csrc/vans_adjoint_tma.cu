@@ -22,6 +22,98 @@
 
 namespace vans {
 
+// One staged tile of the reverse step (the compute warps): read the stage into
+// registers, release it, then the vector-Jacobian product of each cell, the
+// compensated accumulation and the scatter of lambda.  EDGE = false: the
+// tile's row touches no wall, so the wall flags are false at compile time.
+template <int Q, int NT, int CPT, typename T, bool EDGE, class Rel>
+__device__ __forceinline__ void adjoint_tile(const VDom &d, const float *__restrict__ sb,
+                                             const float *__restrict__ lin, float *__restrict__ lout,
+                                             float *__restrict__ grad, const Nb3 &Y, const Nb3 &Z,
+                                             int y, int z, int xs, int tid,
+                                             float (&gs)[CPT][1 + Lat<Q>::D],
+                                             float (&gc)[CPT][1 + Lat<Q>::D], Rel &&release) {
+    using L = Lat<Q>;
+    constexpr int D = L::D;
+    constexpr int TW = NT * CPT;
+    constexpr int SEG = TW + 8;
+    constexpr int NE = EpsRows<Q>::N;
+    const long long nc = (1 + D) * d.cells;
+    const long long ro = row_offset(d, y, z);
+    auto ywall = [&](int k) { return EDGE && Y.wall[k]; };
+    auto zwall = [&](int k) { return EDGE && Z.wall[k]; };
+    float h[CPT][Q], et[CPT][Q], mu[CPT][Q];
+#pragma unroll
+    for (int cc = 0; cc < CPT; ++cc) {
+        const int xl = tid + cc * NT;
+        const int x = xs + xl;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const bool bb = ywall(1 - L::ey(i)) || zwall(1 - L::ez(i));
+            h[cc][i] = sb[i * SEG + 4 + xl + (bb ? 0 : -L::ex(i))];
+        }
+        const float e0 = sb[(Q + eps_slot<Q>(0, 0)) * SEG + 4 + xl];
+        et[cc][0] = e0;
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const bool wall = ywall(1 + L::ey(i)) || zwall(1 + L::ez(i));
+            et[cc][i] = wall ? e0
+                             : sb[(Q + eps_slot<Q>(L::ey(i), L::ez(i))) * SEG + 4 + xl + L::ex(i)];
+        }
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            // lambda of the population this cell sends along e_i; across the
+            // periodic x seam the scatter of the step after left it in the
+            // halo column on the other side, outside this tile's segment
+            const bool wall_out = ywall(1 + L::ey(i)) || zwall(1 + L::ez(i));
+            float v = sb[(Q + NE + i) * SEG + 4 + xl];
+            if (!wall_out && L::ex(i) > 0 && x == d.nx - 1) v = lin[i * d.plane + ro - 1];
+            if (!wall_out && L::ex(i) < 0 && x == 0) v = lin[i * d.plane + ro + d.nx];
+            mu[cc][i] = v;
+        }
+    }
+    release();
+#pragma unroll
+    for (int cc = 0; cc < CPT; ++cc) {
+        const int x = xs + tid + cc * NT;
+        if (x >= d.nx) continue;
+        const float e0 = et[cc][0];
+        float hh[Q], ll[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) hh[i] = h[cc][i];
+        if (EDGE) apply_moving_wall<Q>(d, Y.wall[2], Z, e0, hh);
+        T ebar, gbar[3];
+        collide_vjp_t<Q, T>(d, hh, e0, et[cc], mu[cc], ll, ebar, gbar);
+        if (EDGE && d.moving && Y.wall[2]) {
+            // the populations this cell sends into the moving wall come back
+            // as their opposites with a gain that is linear in eps(x)
+#pragma unroll
+            for (int i = 0; i < Q; ++i)
+                if (L::ey(i) > 0 && !zwall(1 + L::ez(i)))
+                    ebar += (T)wall_gain<Q>(d, L::opp(i), 1.f) * (T)mu[cc][i];
+        }
+        const long long m = ((long long)z * d.ny + y) * d.nx + x;
+        acc2_reg(gs[cc][0], gc[cc][0], (float)ebar);
+#pragma unroll
+        for (int c = 0; c < D; ++c) acc2_reg(gs[cc][1 + c], gc[cc][1 + c], (float)gbar[c]);
+#pragma unroll
+        for (int c = 0; c <= D; ++c) {
+            grad[c * d.cells + m] = gs[cc][c];
+            grad[nc + c * d.cells + m] = gc[cc][c];
+        }
+        // lambda^t goes back to the entry the pull read (the transposed pull)
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int ey = L::ey(i), ez = L::ez(i);
+            const bool bb = ywall(1 - ey) || zwall(1 - ez);
+            if (bb)
+                lout[L::opp(i) * d.plane + ro + x] = ll[i];
+            else
+                lout[i * d.plane + row_offset(d, Y.r[1 - ey], Z.r[1 - ez]) + x - L::ex(i)] = ll[i];
+        }
+    }
+}
+
 template <int Q, int NT, int CPT, typename T>
 __global__ void __launch_bounds__(NT + 32) k_adjoint_tma(const VDom d, const float *__restrict__ st,
                                                          const float *__restrict__ lin,
@@ -112,78 +204,17 @@ __global__ void __launch_bounds__(NT + 32) k_adjoint_tma(const VDom d, const flo
             return;
         }
         const float *sb = buf + s * (NS * SEG);
-        const long long ro = row_offset(d, y, z);
-        float h[CPT][Q], et[CPT][Q], mu[CPT][Q];
-#pragma unroll
-        for (int cc = 0; cc < CPT; ++cc) {
-            const int xl = tid + cc * NT;
-            const int x = xs + xl;
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const bool bb = Y.wall[1 - L::ey(i)] || Z.wall[1 - L::ez(i)];
-                h[cc][i] = sb[i * SEG + 4 + xl + (bb ? 0 : -L::ex(i))];
-            }
-            const float e0 = sb[(Q + eps_slot<Q>(0, 0)) * SEG + 4 + xl];
-            et[cc][0] = e0;
-#pragma unroll
-            for (int i = 1; i < Q; ++i) {
-                const bool wall = Y.wall[1 + L::ey(i)] || Z.wall[1 + L::ez(i)];
-                et[cc][i] = wall ? e0
-                                 : sb[(Q + eps_slot<Q>(L::ey(i), L::ez(i))) * SEG + 4 + xl + L::ex(i)];
-            }
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                // lambda of the population this cell sends along e_i; across the
-                // periodic x seam the scatter of the step after left it in the
-                // halo column on the other side, outside this tile's segment
-                const bool wall_out = Y.wall[1 + L::ey(i)] || Z.wall[1 + L::ez(i)];
-                float v = sb[(Q + NE + i) * SEG + 4 + xl];
-                if (!wall_out && L::ex(i) > 0 && x == d.nx - 1) v = lin[i * d.plane + ro - 1];
-                if (!wall_out && L::ex(i) < 0 && x == 0) v = lin[i * d.plane + ro + d.nx];
-                mu[cc][i] = v;
-            }
-        }
-        __syncwarp();                                 // every lane's reads precede the arrive
-        if (lane == 0) mbar_arrive(&empty[s]);
-#pragma unroll
-        for (int cc = 0; cc < CPT; ++cc) {
-            const int x = xs + tid + cc * NT;
-            if (x >= d.nx) continue;
-            const float e0 = et[cc][0];
-            float hh[Q], ll[Q];
-#pragma unroll
-            for (int i = 0; i < Q; ++i) hh[i] = h[cc][i];
-            apply_moving_wall<Q>(d, Y.wall[2], Z, e0, hh);
-            T ebar, gbar[3];
-            collide_vjp_t<Q, T>(d, hh, e0, et[cc], mu[cc], ll, ebar, gbar);
-            if (d.moving && Y.wall[2]) {
-                // the populations this cell sends into the moving wall come back
-                // as their opposites with a gain that is linear in eps(x)
-#pragma unroll
-                for (int i = 0; i < Q; ++i)
-                    if (L::ey(i) > 0 && !Z.wall[1 + L::ez(i)])
-                        ebar += (T)wall_gain<Q>(d, L::opp(i), 1.f) * (T)mu[cc][i];
-            }
-            const long long m = ((long long)z * d.ny + y) * d.nx + x;
-            acc2_reg(gs[cc][0], gc[cc][0], (float)ebar);
-#pragma unroll
-            for (int c = 0; c < D; ++c) acc2_reg(gs[cc][1 + c], gc[cc][1 + c], (float)gbar[c]);
-#pragma unroll
-            for (int c = 0; c <= D; ++c) {
-                grad[c * d.cells + m] = gs[cc][c];
-                grad[nc + c * d.cells + m] = gc[cc][c];
-            }
-            // lambda^t goes back to the entry the pull read (the transposed pull)
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const int ey = L::ey(i), ez = L::ez(i);
-                const bool bb = Y.wall[1 - ey] || Z.wall[1 - ez];
-                if (bb)
-                    lout[L::opp(i) * d.plane + ro + x] = ll[i];
-                else
-                    lout[i * d.plane + row_offset(d, Y.r[1 - ey], Z.r[1 - ez]) + x - L::ex(i)] = ll[i];
-            }
-        }
+        uint64_t *const emp = &empty[s];
+        auto release = [&] {
+            __syncwarp();                             // every lane's reads precede the arrive
+            if (lane == 0) mbar_arrive(emp);
+        };
+        if (Y.wall[0] || Y.wall[2] || Z.wall[0] || Z.wall[2])
+            adjoint_tile<Q, NT, CPT, T, true>(d, sb, lin, lout, grad, Y, Z, y, z, xs, tid, gs, gc,
+                                              release);
+        else
+            adjoint_tile<Q, NT, CPT, T, false>(d, sb, lin, lout, grad, Y, Z, y, z, xs, tid, gs, gc,
+                                               release);
         if (++s == stages) { s = 0; par ^= 1u; }
     }
 }
