@@ -46,8 +46,8 @@ FALLBACK_HBM_GBS = 6800.0
 # a changed kernel or another shape reports null.
 TRAFFIC = {
     # profiles/launches_bench_4096.md: mean of two launches each
-    (4, 4, 4, 7, "ee9f0a8d9ac48724"): (679592960 + 559588352 + 680115456 + 557359104) // 2,
-    (4, 4, 4, 5, "ee9f0a8d9ac48724"): (681760256 + 559564544 + 681480960 + 556161536) // 2,
+    (4, 4, 4, 7, "16b75753fef84e81"): (679524352 + 559597568 + 680111872 + 557803264) // 2,
+    (4, 4, 4, 5, "16b75753fef84e81"): (681839616 + 559769856 + 681655552 + 556167168) // 2,
 }
 _PIPELINE_SOURCES = ("vans_step_tma.cu", "vans_pipeline.cuh", "vans_device.cuh", "vans_tma.cuh")
 KERNEL_SOURCES = {0: ("vans_step.cu", "vans_device.cuh")}
