@@ -693,12 +693,12 @@ __device__ __forceinline__ void ilv_run(Cur cur, const int *status, int ntiles, 
         bool ok = true;
         for (int k = 0; k < n; ++k) {
             const int s = k % stages;
+            cur.load(ntiles);                         // (its latency hides behind the wait)
             if (k >= stages) {
                 ok = mbar_wait_bounded(&empty[s], (uint32_t)(((k / stages) - 1) & 1));
                 if (!ok) break;
                 fence_proxy_async_smem();
             }
-            cur.load(ntiles);
             issue_tile<Q, TW>(cur.dom(), cur.fin(), cur.row(), cur.xs(TW), buf + s * (NS * SEG),
                               &full[s]);
             issued = k + 1;
@@ -716,11 +716,11 @@ __device__ __forceinline__ void ilv_run(Cur cur, const int *status, int ntiles, 
     int s = 0;
     uint32_t par = 0;
     for (int k = 0; k < n; ++k) {
+        cur.load(ntiles);                             // descriptor loads overlap the wait
         if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[s], par))) {
             if (lane == 0 && st) atomicOr(st, 2);
             return;
         }
-        cur.load(ntiles);
         const VDom &d = cur.dom();
         int y, z;
         Nb3 Y, Z;
