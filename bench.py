@@ -274,6 +274,7 @@ def bench_d3q19(torch, V, W, args=None):
            "steps": n, "value": cells * n / t / 1e6, "unit": "MLUPS",
            "gb_s": BYTES_PER_CELL[19] * cells * n / t / 1e9,
            "launch": vars(L), "launches": s.launch_count - c0}
+    out["frac_of_peak"] = out["gb_s"] / peaks()[0]
     s.close()
     return out
 
@@ -300,6 +301,7 @@ def bench_batched(torch, V, W, args=None):
            "value": cells * n / t / 1e6, "unit": "MLUPS",
            "gb_s": BYTES_PER_CELL[9] * cells * n / t / 1e9,
            "launch": vars(L), "launches": b.launch_count - c0}
+    out["frac_of_peak"] = out["gb_s"] / peaks()[0]
     b.close()
     return out
 
