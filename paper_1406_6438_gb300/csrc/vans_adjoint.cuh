@@ -33,9 +33,15 @@ __device__ __forceinline__ void acc2_reg(float &s, float &c, float x) {
     s = t;
 }
 
+// Square root and reciprocal of the reverse arithmetic: FP64 correctly
+// rounded; FP32 the hardware estimates refined by one Newton step (rcp_nr,
+// sqrt_nr: within about an ulp, without the division's slow-path branch).
 template <typename T> __device__ __forceinline__ T vsqrt(T x);
-template <> __device__ __forceinline__ float vsqrt<float>(float x) { return sqrtf(x); }
+template <> __device__ __forceinline__ float vsqrt<float>(float x) { return x > 0.f ? sqrt_nr(x) : 0.f; }
 template <> __device__ __forceinline__ double vsqrt<double>(double x) { return sqrt(x); }
+template <typename T> __device__ __forceinline__ T vrcp(T x);
+template <> __device__ __forceinline__ float vrcp<float>(float x) { return rcp_nr(x); }
+template <> __device__ __forceinline__ double vrcp<double>(double x) { return 1.0 / x; }
 
 template <int Q, typename T>
 struct MacroT {
@@ -58,7 +64,7 @@ __device__ __forceinline__ void macro_t(const VDom &d, const float h[Q], float e
     M.dl = dl;
     M.e0 = e0;
     M.R = e0 + dl;
-    M.inv_e = T(1) / e0;
+    M.inv_e = vrcp<T>(e0);
     M.rho = M.R * M.inv_e;
 #pragma unroll
     for (int c = 0; c < D; ++c) { M.ge[c] = 0; M.j[c] = 0; }
@@ -96,7 +102,7 @@ __device__ __forceinline__ void macro_t(const VDom &d, const float h[Q], float e
     if (d.drag_mode == 0) { a = b = da = db = 0; }
     if (d.drag_mode == 1) { b = db = 0; }
     M.alpha = a; M.beta = b; M.dalpha = da; M.dbeta = db;
-    const T pc = M.rho / T(3);
+    const T pc = M.rho * (T(1) / T(3));
     M.rho3 = pc;
     T mm2 = 0;
 #pragma unroll
@@ -110,7 +116,7 @@ __device__ __forceinline__ void macro_t(const VDom &d, const float h[Q], float e
     M.mm = vsqrt<T>(mm2);
     M.sq = vsqrt<T>(M.a * M.a + T(4) * M.b * M.mm);
     M.D = M.a + M.sq;
-    M.inv_D = T(1) / M.D;
+    M.inv_D = vrcp<T>(M.D);
     const T s = T(2) * M.inv_D;
     M.un = M.mm * s;
     const T kd = M.alpha + M.beta * M.un;
@@ -141,7 +147,7 @@ __device__ __forceinline__ void macro_vjp_t(const VDom &d, const MacroT<Q, T> &M
     T alphabar = -Fu;
     T betabar = -M.un * Fu;
     const T kd = M.alpha + M.beta * M.un;
-    const T ib = (M.un > T(0)) ? M.beta * Fu / M.un : T(0);
+    const T ib = (M.un > T(0)) ? M.beta * Fu * vrcp<T>(M.un) : T(0);
     // reciprocals formed once (each a correctly rounded division); the
     // quotients below are products with them
     T ubu = 0;
@@ -151,12 +157,12 @@ __device__ __forceinline__ void macro_vjp_t(const VDom &d, const MacroT<Q, T> &M
         ubu += ubar[c] * M.u[c];
     }
     // u = 2 m / D,  D = a + sqrt(a^2 + 4 b |m|)
-    const T inv_sq = T(1) / M.sq;
+    const T inv_sq = vrcp<T>(M.sq);
     const T Dbar = -ubu * M.inv_D;
     const T abar = Dbar * (T(1) + M.a * inv_sq);
     const T bbar = Dbar * T(2) * M.mm * inv_sq;
     const T mmbar = Dbar * T(2) * M.b * inv_sq;
-    const T im = (M.mm > T(0)) ? mmbar / M.mm : T(0);
+    const T im = (M.mm > T(0)) ? mmbar * vrcp<T>(M.mm) : T(0);
     const T s2 = T(2) * M.inv_D;
 #pragma unroll
     for (int c = 0; c < D; ++c) mbar[c] = ubar[c] * s2 + im * M.m[c];
@@ -174,7 +180,7 @@ __device__ __forceinline__ void macro_vjp_t(const VDom &d, const MacroT<Q, T> &M
         pg += Pcbar[c] * M.ge[c];
         gbar[c] = M.rho3 * Pcbar[c];
     }
-    const T rhobar = pg / T(3);
+    const T rhobar = pg * (T(1) / T(3));
     // rho = R / eps
     Rbar += rhobar * M.inv_e;
     ebar = -rhobar * M.rho * M.inv_e;
