@@ -1,5 +1,6 @@
 // vans_aux.cu -- everything around the step: porosity set-up, moments, state
-// import/export, divergence check, outlet flux, and the reverse-mode adjoint.
+// import/export, divergence check, outlet flux, and the register-load form of
+// the reverse-mode adjoint step (the pipelined one is in vans_adjoint_tma.cu).
 #include "vans_adjoint.cuh"
 #include "vans_device.cuh"
 

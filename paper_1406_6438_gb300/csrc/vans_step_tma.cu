@@ -2,16 +2,32 @@
 //
 // Same arithmetic as k_step (vans_step.cu) -- pull, moments, implicit velocity,
 // f^eq + P_i + F_i, relax, store -- but the loads no longer come from the
-// threads.  A persistent CTA owns a contiguous run of tiles (TW cells of one
-// row); one elected thread streams the Q source-row segments and the porosity
-// rows of the next tiles into shared memory with 1-D cp.async.bulk copies that
-// complete on an mbarrier, while all threads compute the current tile from
-// shared memory.  Copies therefore stay in flight through the compute phase,
-// which is what limited the register-load version (one load phase per warp,
-// then ~1100 instructions with nothing in flight).  Shared-memory reads are
-// unit-stride across a warp (no bank conflicts) and the +-1 column shift of the
-// pull is just an offset.  Stores go straight to global memory, 128 bytes per
-// warp instruction.
+// threads: one elected thread streams the Q source-row segments of a row tile
+// and its porosity rows into shared memory with 1-D cp.async.bulk copies that
+// complete on an mbarrier (transaction bytes), `stages` tiles ahead, while the
+// compute threads work on the current tile from shared memory.  Copies stay in
+// flight through the compute phase, which is what limited the register-load
+// kernel (one load phase per warp, then ~1100 instructions with nothing in
+// flight).  Shared-memory reads are unit-stride across a warp and the +-1
+// column shift of the pull is an offset.  The launch kinds of this file:
+//
+//   1  k_step_tma: persistent CTAs over contiguous runs of tiles, porosity
+//      rows staged per tile; a block barrier before each refill.
+//   2  k_step_tma_ring: each CTA walks a strip of consecutive rows of one
+//      column block and keeps the porosity rows in a shared-memory ring (each
+//      row leaves HBM once per strip).
+//   3  kind 2 with each thread on V adjacent cells (16- or 8-byte shared loads
+//      and global stores).
+//   4, 5  kinds 2, 3 warp-specialised: a producer warp refills a stage when
+//      every compute warp has released it on an "empty" mbarrier, which each
+//      warp does right after reading the stage into registers.
+//   6, 7  k_step_tma_ilv: persistent CTAs take tiles b, b+G, ... of the
+//      row-major order (the whole grid sweeps one band of rows), warp-
+//      specialised as 4/5; 6 strided cells, 7 adjacent cells.
+//
+// The batched step (kinds 2, 4-7 over many domains) uses the same tile bodies
+// with a strip table or an interleaved tile table; plates-on-nodes instances
+// (wall_kind 1) exist for a subset of the launch shapes.
 #include "vans_pipeline.cuh"
 
 namespace vans {
