@@ -17,6 +17,21 @@ def poiseuille_series(y, t, g, nu, H, nterms=400):
     return u
 
 
+def duct_series(y, z, g, nu, A, B, nterms=200):
+    """Steady laminar flow along x in the rectangular duct 0 < y < A, 0 < z < B
+    (no slip on all four walls) driven by g: nu (u_yy + u_zz) = -g.  Sine series
+    in y of the plane-channel parabola, each mode corrected by the cosh term
+    that brings it to zero on the z walls:
+    u = sum_{n odd} 4 g A^2/(nu n^3 pi^3) sin(n pi y/A)
+        [1 - cosh(n pi (z - B/2)/A) / cosh(n pi B/(2A))]."""
+    u = np.zeros(np.broadcast(y, z).shape)
+    for n in range(1, 2 * nterms, 2):
+        k = n * np.pi / A
+        u = u + 4 * g * A * A / (nu * n ** 3 * np.pi ** 3) * np.sin(k * y) \
+            * (1 - np.cosh(k * (z - B / 2)) / np.cosh(k * B / 2))
+    return u
+
+
 def brinkman(y, g, nu, eps, K, H):
     """Steady solution of nu u'' - (eps nu/K) u + g = 0, u(0) = u(H) = 0."""
     r = np.sqrt(eps / K)

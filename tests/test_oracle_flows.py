@@ -5,7 +5,7 @@ import pytest
 
 import oracle as O
 from paper_1406_6438_gb300 import workloads as W
-from tests._closed_forms import brinkman, porous_bvp, poiseuille_series
+from tests._closed_forms import brinkman, duct_series, porous_bvp, poiseuille_series
 
 CS2 = 1.0 / 3.0
 
@@ -62,6 +62,31 @@ def test_poiseuille_exact_at_magic_tau(q):
     prof = u[0, 0, :, 0]
     assert np.abs(prof - ex).max() <= 1e-10 * ex.max()
     assert np.abs(u[1]).max() <= 1e-14
+
+
+def test_d3q19_duct_flow_against_the_series_solution():
+    """D3Q19, eps = 1, no drag, half-way bounce-back on the y and z walls of a
+    square duct (the directions that cross a y and a z wall at once bounce back
+    plainly): the steady profile against the series solution of nu lap u = -g
+    at the nodes (j + 1/2, k + 1/2), at tau = 1/2 + sqrt(3/16).  The corners
+    leave a second-order error: within 4e-3 of the maximum at H = 8 and 1e-3 at
+    H = 16, falling by more than 3.5x per halving of the spacing."""
+    tau = 0.5 + np.sqrt(3.0 / 16.0)
+    nu = CS2 * (tau - 0.5)
+    g = 1e-6
+    errs = []
+    for H in (8, 16):
+        p = O.Params(q=19, nx=2, ny=H, nz=H, wall_mask=6, tau=tau, g=(g, 0, 0))
+        eps = np.ones(p.shape)
+        f = O.run(p, eps, O.init(p, eps), int(6 * H * H / nu))
+        _, u = O.moments(p, eps, f)
+        c = np.arange(H) + 0.5
+        Z, Y = np.meshgrid(c, c, indexing="ij")
+        ex = duct_series(Y, Z, g, nu, H, H)
+        errs.append(np.abs(u[0, :, :, 0] - ex).max() / ex.max())
+        assert np.abs(u[1:]).max() <= 1e-5 * ex.max()
+    assert errs[0] <= 4e-3 and errs[1] <= 1e-3
+    assert errs[0] / errs[1] >= 3.5
 
 
 def test_poiseuille_startup_series():
