@@ -74,3 +74,22 @@ def test_batched_equals_single_domain_solver(L):
         s.launch = L
         s.step(130)
         assert (s.populations() - b.populations(d)).abs().max().item() <= 6e-8
+
+
+@pytest.mark.parametrize("L", [Launch(4, 4, 1), Launch(2, 4, 2, 4), Launch(4, 4, 2, 7),
+                               Launch(2, 8, 2, 6)])
+def test_batched_domains_with_moving_walls(L):
+    """Domains whose upper wall moves (each at its own speed) next to resting
+    ones in one batch: populations of every domain against the oracle."""
+    torch = torch_cuda()
+    doms = W.batched_channels(n=4, seed=45, nx_range=(30, 600), ny_range=(5, 50))
+    speeds = [0.02, 0.0, 0.008, 0.015]
+    doms = [(dict(p, u_wall=(W.f32(v), 0.0, 0.0)), e) for (p, e), v in zip(doms, speeds)]
+    b = _batch(doms)
+    b.launch = L
+    b.step(60)
+    torch.cuda.synchronize()
+    for d, (p, eps) in enumerate(doms):
+        _, u_o, f_o = oracle_run(p, eps, 60)
+        f = b.populations(d).cpu().numpy()
+        assert np.abs(f - f_o).max() <= 5e-7, (L, d)
