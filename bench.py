@@ -46,8 +46,8 @@ FALLBACK_HBM_GBS = 6800.0
 # a changed kernel or another shape reports null.
 TRAFFIC = {
     # profiles/launches_bench_4096.md: mean of two launches each
-    (4, 4, 4, 7, "16b75753fef84e81"): (679524352 + 559597568 + 680111872 + 557803264) // 2,
-    (4, 4, 4, 5, "16b75753fef84e81"): (681839616 + 559769856 + 681655552 + 556167168) // 2,
+    (4, 4, 4, 7, "e52e6eeeb5a6e453"): (679681280 + 559591680 + 680201216 + 558026752) // 2,
+    (4, 4, 4, 5, "e52e6eeeb5a6e453"): (681838080 + 559746304 + 681529088 + 556450304) // 2,
 }
 _PIPELINE_SOURCES = ("vans_step_tma.cu", "vans_pipeline.cuh", "vans_device.cuh", "vans_tma.cuh")
 KERNEL_SOURCES = {0: ("vans_step.cu", "vans_device.cuh")}
