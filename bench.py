@@ -42,12 +42,12 @@ FALLBACK_HBM_GBS = 6800.0
 
 # DRAM bytes per launch of the step kernel measured by ncu on the 4096^2
 # workload (dram__bytes_read.sum + dram__bytes_write.sum), keyed by launch shape
-# (cpt, warps, rows, kind) and a hash of the kernel sources they were taken on;
-# a changed kernel or another shape reports null.
+# (cpt, warps, rows, kind, ctas) and a hash of the kernel sources they were
+# taken on; a changed kernel or another shape reports null.
 TRAFFIC = {
     # profiles/launches_bench_4096.md: mean of two launches each
-    (4, 4, 4, 7, "e52e6eeeb5a6e453"): (679681280 + 559591680 + 680201216 + 558026752) // 2,
-    (4, 4, 4, 5, "e52e6eeeb5a6e453"): (681838080 + 559746304 + 681529088 + 556450304) // 2,
+    (4, 4, 3, 7, 2, "dd1f983c0e8dae81"): (677230336 + 561260288 + 677409280 + 559662848) // 2,
+    (4, 4, 4, 7, 0, "dd1f983c0e8dae81"): (677272832 + 561345536 + 677409792 + 559596288) // 2,
 }
 _PIPELINE_SOURCES = ("vans_step_tma.cu", "vans_pipeline.cuh", "vans_device.cuh", "vans_tma.cuh")
 KERNEL_SOURCES = {0: ("vans_step.cu", "vans_device.cuh")}
@@ -420,7 +420,7 @@ def main():
     per_launch = t / args.steps
     peak, peak_kind = peaks()
     achieved = BYTES_PER_CELL[9] * cells / per_launch / 1e9
-    key = (L.cpt, L.warps, L.rows, L.kind, kernel_hash(L.kind))
+    key = (L.cpt, L.warps, L.rows, L.kind, L.ctas, kernel_hash(L.kind))
     traffic = TRAFFIC.get(key) if args.n == 4096 else None
 
     # end to end through the public API with host buffers: upload eps from

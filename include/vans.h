@@ -107,14 +107,18 @@ typedef struct {
  *         tile order (the whole grid sweeps one band of rows), porosity rows
  *         staged per tile, producer warp as in kinds 4, 5; 6 strided cells
  *         (D2Q9 cpt 2, D3Q19 cpt 1; warps 4 or 8), 7 consecutive cells as in
- *         kind 3.  Single-domain solver only.
+ *         kind 3.
  *         The batched path takes kinds 0, 2, 4 and 5 (one CTA per strip of
- *         up to 32 rows of one domain; kind 5 D2Q9 only). */
+ *         up to 32 rows of one domain) and 6, 7 (one table of every domain's
+ *         row tiles); the batch is D2Q9 only. */
 typedef struct {
     int cpt;
     int warps;
     int rows;
     int kind;
+    int ctas;   /* kinds 1-7: at most this many CTAs per SM (1..4; the
+                   dynamic shared memory request is raised until no more
+                   fit), 0 = as many as fit; kind 0: must be 0 */
 } vans_launch;
 
 /* ---------------------------------------------------------------- sizes -- */
@@ -245,7 +249,7 @@ int vans_adjoint_segment(vans_t h, const float *ckpt, float *seg, int len, float
  * warps).  kind 1 (the default, cpt 1, 4 warps, 4 stages): bulk-copy pipeline
  * with a producer warp, persistent CTAs over the row tiles; `warps` compute
  * warps (D2Q9: 2 with cpt 1, or 4 with cpt 1 or 2; D3Q19: 4 with cpt 1),
- * `rows` = pipeline stages (2..8).  VANS_ERR_ARG otherwise. */
+ * `rows` = pipeline stages (2..8); ctas must be 0.  VANS_ERR_ARG otherwise. */
 int vans_set_adjoint_launch(vans_t h, const vans_launch *cfg);
 
 /* Arithmetic of the per-cell reverse step: 32 (FP32, the default) or 64 (FP64;
@@ -289,7 +293,7 @@ long long vans_batch_cells(vans_t h);
  * buffers, the padded copy of eps (dense nx*ny*nz floats, 0 < eps <= 1; not
  * range-checked here), is a 16 MiB array that the library holds in device
  * memory on every GPU where it is loaded, until the process exits.
- * Limit: ny*nz rows times the padded row length (nx rounded up to 128, plus 5,
+ * Limit: ny*nz rows times the padded row length (nx rounded up to 128, plus 9,
  * rounded up to 32 floats) must not exceed 4 Mi floats, e.g. up to about a
  * 2000 x 2000 D2Q9 or a 150^3 D3Q19 domain; larger domains get VANS_ERR_ARG.
  * Parameter errors as in vans_create.  The first call on a device looks up the

@@ -39,7 +39,7 @@ class _CParams(ctypes.Structure):
 
 class _CLaunch(ctypes.Structure):
     _fields_ = [("cpt", ctypes.c_int), ("warps", ctypes.c_int), ("rows", ctypes.c_int),
-                ("kind", ctypes.c_int)]
+                ("kind", ctypes.c_int), ("ctas", ctypes.c_int)]
 
 
 @dataclass
@@ -90,15 +90,19 @@ class Params:
 
 @dataclass
 class Launch:
-    """kind 0: register-load kernel (cpt cells per lane, warps x rows per block);
-    kind 1: bulk-copy pipeline (32*warps threads, cpt cells per thread per tile,
-    rows = pipeline stages); kind 2: pipeline over row strips with a porosity
-    ring; kind 3: kind 2 with 4 contiguous cells per thread (D2Q9); kinds 4, 5:
-    kinds 2, 3 with a producer warp and per-warp stage release."""
+    """``vans_launch`` (see include/vans.h).  kind 0: register-load kernel (cpt
+    cells per lane, warps x rows per block); kind 1: bulk-copy pipeline
+    (32*warps threads, cpt cells per thread per tile, rows = pipeline stages);
+    kind 2: pipeline over row strips with a porosity ring; kind 3: kind 2 with
+    consecutive cells per thread; kinds 4, 5: kinds 2, 3 with a producer warp
+    and per-warp stage release; kinds 6, 7: persistent CTAs over interleaved
+    row tiles.  ctas: at most that many CTAs per SM for kinds 1-7 (0: as many
+    as fit)."""
     cpt: int
     warps: int
     rows: int
     kind: int = 0
+    ctas: int = 0
 
 
 _lib = None
@@ -323,17 +327,17 @@ class Solver:
     def autotune(self) -> Launch:
         c = _CLaunch()
         _check(self.lib.vans_autotune(self._h, ctypes.byref(c)), "vans_autotune")
-        return Launch(c.cpt, c.warps, c.rows, c.kind)
+        return Launch(c.cpt, c.warps, c.rows, c.kind, c.ctas)
 
     @property
     def launch(self) -> Launch:
         c = _CLaunch()
         _check(self.lib.vans_get_launch(self._h, ctypes.byref(c)), "vans_get_launch")
-        return Launch(c.cpt, c.warps, c.rows, c.kind)
+        return Launch(c.cpt, c.warps, c.rows, c.kind, c.ctas)
 
     @launch.setter
     def launch(self, L: Launch):
-        c = _CLaunch(int(L.cpt), int(L.warps), int(L.rows), int(L.kind))
+        c = _CLaunch(int(L.cpt), int(L.warps), int(L.rows), int(L.kind), int(L.ctas))
         _check(self.lib.vans_set_launch(self._h, ctypes.byref(c)), "vans_set_launch")
 
     @property
@@ -368,7 +372,7 @@ class Solver:
                "vans_step_adjoint")
 
     def set_adjoint_launch(self, L: Launch):
-        c = _CLaunch(int(L.cpt), int(L.warps), int(L.rows), int(L.kind))
+        c = _CLaunch(int(L.cpt), int(L.warps), int(L.rows), int(L.kind), int(L.ctas))
         _check(self.lib.vans_set_adjoint_launch(self._h, ctypes.byref(c)), "vans_set_adjoint_launch")
 
     def set_adjoint_precision(self, bits: int):
@@ -456,17 +460,17 @@ class Batch:
     def autotune(self) -> Launch:
         c = _CLaunch()
         _check(self.lib.vans_batch_autotune(self._h, ctypes.byref(c)), "vans_batch_autotune")
-        return Launch(c.cpt, c.warps, c.rows, c.kind)
+        return Launch(c.cpt, c.warps, c.rows, c.kind, c.ctas)
 
     @property
     def launch(self) -> Launch:
         c = _CLaunch()
         _check(self.lib.vans_get_launch(self._h, ctypes.byref(c)), "vans_get_launch")
-        return Launch(c.cpt, c.warps, c.rows, c.kind)
+        return Launch(c.cpt, c.warps, c.rows, c.kind, c.ctas)
 
     @launch.setter
     def launch(self, L: Launch):
-        c = _CLaunch(int(L.cpt), int(L.warps), int(L.rows), int(L.kind))
+        c = _CLaunch(int(L.cpt), int(L.warps), int(L.rows), int(L.kind), int(L.ctas))
         _check(self.lib.vans_set_launch(self._h, ctypes.byref(c)), "vans_set_launch")
 
     @property

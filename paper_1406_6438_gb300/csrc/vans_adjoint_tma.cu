@@ -36,7 +36,7 @@ __device__ __forceinline__ void adjoint_tile(const VDom &d, const float *__restr
     using L = Lat<Q>;
     constexpr int D = L::D;
     constexpr int TW = NT * CPT;
-    constexpr int SEG = TW + 8;
+    constexpr int SEG = TW + 2 * kLead;
     constexpr int NE = EpsRows<Q>::N;
     const long long nc = (1 + D) * d.cells;
     const long long ro = row_offset(d, y, z);
@@ -50,15 +50,15 @@ __device__ __forceinline__ void adjoint_tile(const VDom &d, const float *__restr
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const bool bb = ywall(1 - L::ey(i)) || zwall(1 - L::ez(i));
-            h[cc][i] = sb[i * SEG + 4 + xl + (bb ? 0 : -L::ex(i))];
+            h[cc][i] = sb[i * SEG + kLead + xl + (bb ? 0 : -L::ex(i))];
         }
-        const float e0 = sb[(Q + eps_slot<Q>(0, 0)) * SEG + 4 + xl];
+        const float e0 = sb[(Q + eps_slot<Q>(0, 0)) * SEG + kLead + xl];
         et[cc][0] = e0;
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
             const bool wall = ywall(1 + L::ey(i)) || zwall(1 + L::ez(i));
             et[cc][i] = wall ? e0
-                             : sb[(Q + eps_slot<Q>(L::ey(i), L::ez(i))) * SEG + 4 + xl + L::ex(i)];
+                             : sb[(Q + eps_slot<Q>(L::ey(i), L::ez(i))) * SEG + kLead + xl + L::ex(i)];
         }
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
@@ -66,7 +66,7 @@ __device__ __forceinline__ void adjoint_tile(const VDom &d, const float *__restr
             // periodic x seam the scatter of the step after left it in the
             // halo column on the other side, outside this tile's segment
             const bool wall_out = ywall(1 + L::ey(i)) || zwall(1 + L::ez(i));
-            float v = sb[(Q + NE + i) * SEG + 4 + xl];
+            float v = sb[(Q + NE + i) * SEG + kLead + xl];
             if (!wall_out && L::ex(i) > 0 && x == d.nx - 1) v = lin[i * d.plane + ro - 1];
             if (!wall_out && L::ex(i) < 0 && x == 0) v = lin[i * d.plane + ro + d.nx];
             mu[cc][i] = v;
@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(NT + 32) k_adjoint_tma(const VDom d, const flo
     using L = Lat<Q>;
     constexpr int D = L::D;
     constexpr int TW = NT * CPT;
-    constexpr int SEG = TW + 8;
+    constexpr int SEG = TW + 2 * kLead;
     constexpr int NE = EpsRows<Q>::N;
     constexpr int NS = 2 * Q + NE;      // state rows, porosity rows, lambda rows
     constexpr int NCW = NT / 32;
@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(NT + 32) k_adjoint_tma(const VDom d, const flo
             const long long ro = row_offset(d, row % d.ny, row / d.ny);
 #pragma unroll
             for (int i = 0; i < Q; ++i)
-                bulk_g2s(sb + (Q + NE + i) * SEG, lin + i * d.plane + ro + xs - 4, bytes, &full[s]);
+                bulk_g2s(sb + (Q + NE + i) * SEG, lin + i * d.plane + ro + xs - kLead, bytes, &full[s]);
             issued = k + 1;
         }
         if (!ok) {
@@ -224,7 +224,7 @@ static cudaError_t launch_adj_tma_t(const VDom &d, const float *state, const flo
                                     float *lam_out, float *grad, int stages, cudaStream_t s) {
     constexpr int TW = NT * CPT;
     constexpr int NS = 2 * Q + EpsRows<Q>::N;
-    const size_t smem = kBarBytes + (size_t)stages * NS * (TW + 8) * sizeof(float);
+    const size_t smem = kBarBytes + (size_t)stages * NS * (TW + 2 * kLead) * sizeof(float);
     if (stages < 2 || stages > kBarBytes / 16 || smem > 227 * 1024) return cudaErrorInvalidValue;
     auto kern = k_adjoint_tma<Q, NT, CPT, T>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <new>
+#include <iterator>
 #include <vector>
 
 #include "vans.h"
@@ -114,7 +115,9 @@ void fill_dom(const vans_params *p, VDom &d) {
 bool launch_ok(const vans_launch *c, int q, bool batched) {
     if (!c) return false;
     if (c->cpt != 1 && c->cpt != 2 && c->cpt != 4) return false;
+    if (c->ctas < 0 || c->ctas > 4) return false;
     if (c->kind == 0) {
+        if (c->ctas != 0) return false;
         if (c->warps < 1 || c->warps > 8 || c->rows < 1 || c->rows > 8) return false;
         return c->warps * c->rows <= 8;
     }
@@ -369,8 +372,9 @@ std::vector<Launch> candidates(int q, bool batched) {
         const Launch t[] = {{2, 4, 3, 2}, {4, 4, 2, 2}, {4, 4, 3, 2}, {2, 8, 2, 2}, {2, 8, 3, 2},
                             {1, 8, 3, 2}, {2, 8, 2, 4}, {2, 4, 2, 4}, {4, 2, 2, 5}, {4, 2, 3, 5},
                             {4, 4, 2, 5}, {4, 4, 3, 5}, {4, 4, 4, 5}, {2, 4, 2, 6}, {2, 8, 2, 6},
-                            {4, 2, 4, 7}, {4, 2, 3, 7}, {4, 4, 2, 7}, {4, 4, 4, 7}};
-        c.insert(c.end(), t, t + 19);
+                            {4, 2, 4, 7}, {4, 2, 3, 7}, {4, 4, 2, 7}, {4, 4, 4, 7},
+                            {4, 4, 2, 5, 2}, {4, 4, 2, 7, 2}, {4, 4, 3, 7, 2}};
+        c.insert(c.end(), std::begin(t), std::end(t));
         return c;
     }
     // bulk-copy pipeline shapes {cpt, warps, stages, kind}
@@ -382,16 +386,19 @@ std::vector<Launch> candidates(int q, bool batched) {
                             {4, 2, 3, 3}, {4, 2, 4, 3}, {2, 8, 2, 4}, {4, 4, 2, 4},
                             {4, 2, 2, 5}, {4, 4, 2, 5}, {4, 4, 4, 5}, {4, 4, 5, 5},
                             {4, 4, 6, 5}, {2, 8, 2, 6}, {2, 4, 2, 6}, {4, 4, 4, 7},
-                            {4, 2, 4, 7}, {4, 4, 2, 7}};
-        c.insert(c.end(), t, t + 30);
+                            {4, 2, 4, 7}, {4, 4, 2, 7}, {4, 4, 2, 5, 2}, {4, 4, 3, 5, 2},
+                            {4, 4, 2, 7, 2}, {4, 4, 3, 7, 2}, {4, 4, 2, 7, 3}};
+        c.insert(c.end(), std::begin(t), std::end(t));
     } else {
         const Launch t[] = {{1, 4, 3, 1}, {1, 4, 4, 1}, {2, 4, 2, 1}, {2, 4, 3, 1},
                             {1, 8, 2, 1}, {1, 8, 3, 1}, {1, 4, 3, 2}, {2, 4, 2, 2},
                             {2, 4, 3, 2}, {1, 8, 2, 2}, {1, 8, 3, 2}, {1, 4, 3, 4},
                             {1, 8, 2, 4}, {2, 4, 2, 3}, {2, 4, 3, 3}, {2, 2, 3, 3},
                             {2, 4, 2, 5}, {2, 4, 3, 5}, {2, 4, 4, 5}, {2, 2, 3, 5},
-                            {1, 4, 3, 6}, {1, 8, 3, 6}, {2, 4, 3, 7}, {2, 2, 3, 7}};
-        c.insert(c.end(), t, t + 24);
+                            {1, 4, 3, 6}, {1, 8, 3, 6}, {2, 4, 3, 7}, {2, 2, 3, 7},
+                            {2, 4, 2, 7}, {2, 4, 2, 7, 2}, {2, 4, 2, 7, 1}, {2, 4, 3, 7, 1},
+                            {2, 4, 3, 7, 2}, {2, 4, 2, 3, 2}, {2, 4, 2, 5, 2}};
+        c.insert(c.end(), std::begin(t), std::end(t));
     }
     return c;
 }
@@ -585,15 +592,14 @@ int vans_get_launch(vans_t h, vans_launch *cfg) {
     cfg->warps = h->L.warps;
     cfg->rows = h->L.rows;
     cfg->kind = h->L.kind;
+    cfg->ctas = h->L.ctas;
     return VANS_OK;
 }
 
 int vans_set_launch(vans_t h, const vans_launch *cfg) {
     if (!h || !launch_ok(cfg, h->q, h->batched)) return VANS_ERR_ARG;
-    if (!h->batched && h->dom.nee && !vans::launch_has_plates(h->q, Launch{cfg->cpt, cfg->warps,
-                                                                          cfg->rows, cfg->kind}))
-        return VANS_ERR_UNSUPPORTED;
-    const Launch L{cfg->cpt, cfg->warps, cfg->rows, cfg->kind};
+    const Launch L{cfg->cpt, cfg->warps, cfg->rows, cfg->kind, cfg->ctas};
+    if (!h->batched && h->dom.nee && !vans::launch_has_plates(h->q, L)) return VANS_ERR_UNSUPPORTED;
     if (h->batched) return set_batch_launch(h, L);
     h->L = L;
     drop_graph(h);
@@ -629,6 +635,7 @@ int vans_autotune(vans_t h, vans_launch *chosen) {
         chosen->warps = best.warps;
         chosen->rows = best.rows;
         chosen->kind = best.kind;
+        chosen->ctas = best.ctas;
     }
     return VANS_OK;
 }
@@ -723,7 +730,7 @@ int vans_adjoint_segment(vans_t h, const float *ckpt, float *seg, int len, float
 }
 
 int vans_set_adjoint_launch(vans_t h, const vans_launch *cfg) {
-    if (!h || h->batched || !cfg) return VANS_ERR_ARG;
+    if (!h || h->batched || !cfg || cfg->ctas != 0) return VANS_ERR_ARG;
     if (cfg->kind == 0) {
         if (cfg->warps < 1 || cfg->rows < 1 || cfg->warps * cfg->rows > 8) return VANS_ERR_ARG;
         if (!(cfg->cpt == 1 || (cfg->cpt == 2 && h->q == 9))) return VANS_ERR_ARG;
@@ -947,6 +954,7 @@ int vans_batch_autotune(vans_t h, vans_launch *chosen) {
         chosen->warps = best.warps;
         chosen->rows = best.rows;
         chosen->kind = best.kind;
+        chosen->ctas = best.ctas;
     }
     return VANS_OK;
 }

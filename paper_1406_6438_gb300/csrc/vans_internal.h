@@ -5,7 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#define VANS_OFF 4  // column 0 of a padded row sits 4 floats (16 bytes) into the row
+#define VANS_OFF 8  // column 0 of a padded row sits 8 floats (one 32-byte sector) into the row
 
 namespace vans {
 
@@ -46,8 +46,10 @@ struct Tile {
 // kind 0: register-load kernel k_step (cpt cells per lane, warps x rows per block)
 // kind 1: bulk-copy pipeline k_step_tma (32*warps threads, cpt cells per thread
 //         per tile, rows = pipeline stages)
+// ctas: at most that many CTAs per SM for kinds 1-7 (0: as many as fit)
 struct Launch {
     int cpt, warps, rows, kind;
+    int ctas;
 };
 
 // ------------------------------------------------------ kernel launchers ----

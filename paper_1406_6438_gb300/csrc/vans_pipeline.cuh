@@ -36,6 +36,17 @@ __device__ __forceinline__ void row_nbs(const VDom &d, int row, int &y, int &z, 
 
 constexpr int kBarBytes = 128;   // room for up to 16 mbarriers in front of the stages
 
+// A staged row segment of the tile at column xs holds columns xs - kLead ..
+// xs + TW + kLead - 1: the +-1 neighbours of the tile's cells (halo columns
+// included), from and to whole 32-byte sectors (column 0 starts a sector, so
+// column xs - kLead starts one too); a stage slot is TW + 2 kLead floats.
+constexpr int kLead = 8;
+
+// bytes of the copy of one staged row segment with nval cells
+__host__ __device__ constexpr uint32_t seg_bytes(int nval) {
+    return (uint32_t)(((nval + kLead - 1) / kLead * kLead + 2 * kLead) * 4);
+}
+
 // Issue the bulk copies of the tile (row, xs) into stage buffer sb (one
 // thread): the Q population rows the pull reads and the porosity rows.  The
 // barrier's transaction count also covers `extra` further copies of the same
@@ -44,15 +55,13 @@ template <int Q, int TW>
 __device__ __forceinline__ uint32_t issue_tile(const VDom &d, const float *__restrict__ fin, int row,
                                                int xs, float *sb, uint64_t *bar, int extra = 0) {
     using L = Lat<Q>;
-    constexpr int SEG = TW + 8;
+    constexpr int SEG = TW + 2 * kLead;
     constexpr int NS = Q + EpsRows<Q>::N;
     int y, z;
     Nb3 Y, Z;
     row_nbs<Q>(d, row, y, z, Y, Z);
     const int nval = min(TW, d.nx - xs);
-    // columns xs-4 .. xs+round4(nval)+3: the cells, the +-1 neighbours (halo
-    // columns included) and 16-byte alignment on both ends
-    const uint32_t bytes = (uint32_t)((((nval + 3) & ~3) + 8) * 4);
+    const uint32_t bytes = seg_bytes(nval);
     mbar_arrive_expect_tx(bar, bytes * (NS + extra));
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -60,7 +69,7 @@ __device__ __forceinline__ uint32_t issue_tile(const VDom &d, const float *__res
         const bool bb = Y.wall[1 - ey] || Z.wall[1 - ez];
         const int si = bb ? L::opp(i) : i;
         const long long ro = bb ? row_offset(d, y, z) : row_offset(d, Y.r[1 - ey], Z.r[1 - ez]);
-        bulk_g2s(sb + i * SEG, fin + si * d.plane + ro + xs - 4, bytes, bar);
+        bulk_g2s(sb + i * SEG, fin + si * d.plane + ro + xs - kLead, bytes, bar);
     }
     // the porosity rows are read again by the tiles of the neighbouring rows:
     // keep them in L2 longest
@@ -70,7 +79,7 @@ __device__ __forceinline__ uint32_t issue_tile(const VDom &d, const float *__res
 #pragma unroll
         for (int dy = -1; dy <= 1; ++dy) {
             if (Q == 9 && dz != 0) continue;
-            const float *src = d.eps + row_offset(d, Y.r[1 + dy], Z.r[1 + dz]) + xs - 4;
+            const float *src = d.eps + row_offset(d, Y.r[1 + dy], Z.r[1 + dz]) + xs - kLead;
             bulk_g2s_hint(sb + (Q + eps_slot<Q>(dy, dz)) * SEG, src, bytes, bar, again);
         }
     return bytes;

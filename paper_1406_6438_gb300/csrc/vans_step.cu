@@ -156,14 +156,14 @@ __device__ __forceinline__ void step_row(const VDom &d, const float *__restrict_
     if (x0 == 0) {
 #pragma unroll
         for (int i = 0; i < Q; ++i)
-            if (L::ex(i) < 0) fout[i * d.plane + ro + d.nx] = out[i][0];
+            if (L::ex(i) < 0) store_halo_hi<Q>(fout + i * d.plane + ro, d.nx, out[i][0]);
     }
 #pragma unroll
     for (int k = 0; k < CPT; ++k) {
         if (x0 + k == d.nx - 1) {
 #pragma unroll
             for (int i = 0; i < Q; ++i)
-                if (L::ex(i) > 0) fout[i * d.plane + ro - 1] = out[i][k];
+                if (L::ex(i) > 0) store_halo_lo<Q>(fout + i * d.plane + ro, out[i][k]);
         }
     }
     if (plo || phi) store_plates<Q, CPT>(d, fout, y, z, x0, plo, phi, lo, hi);

@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(NT) k_step_tma(const VDom d, const float *__re
                                                  int stages) {
     using L = Lat<Q>;
     constexpr int TW = NT * CPT;
-    constexpr int SEG = TW + 8;
+    constexpr int SEG = TW + 2 * kLead;
     constexpr int NS = Q + EpsRows<Q>::N;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
@@ -87,15 +87,15 @@ __global__ void __launch_bounds__(NT) k_step_tma(const VDom d, const float *__re
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 const bool bb = Y.wall[1 - L::ey(i)] || Z.wall[1 - L::ez(i)];
-                h[i] = sb[i * SEG + 4 + xl + (bb ? 0 : -L::ex(i))];
+                h[i] = sb[i * SEG + kLead + xl + (bb ? 0 : -L::ex(i))];
             }
-            const float e0 = sb[(Q + eps_slot<Q>(0, 0)) * SEG + 4 + xl];
+            const float e0 = sb[(Q + eps_slot<Q>(0, 0)) * SEG + kLead + xl];
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 const bool wall = Y.wall[1 + L::ey(i)] || Z.wall[1 + L::ez(i)];
                 et[i] = (i == 0 || wall)
                             ? e0
-                            : sb[(Q + eps_slot<Q>(L::ey(i), L::ez(i))) * SEG + 4 + xl + L::ex(i)];
+                            : sb[(Q + eps_slot<Q>(L::ey(i), L::ez(i))) * SEG + kLead + xl + L::ex(i)];
             }
             apply_moving_wall<Q>(d, Y.wall[2], Z, e0, h);
             collide<Q>(d, h, e0, et, o);
@@ -105,12 +105,12 @@ __global__ void __launch_bounds__(NT) k_step_tma(const VDom d, const float *__re
                 if (x == 0) {
 #pragma unroll
                     for (int i = 0; i < Q; ++i)
-                        if (L::ex(i) < 0) fout[i * d.plane + ro + d.nx] = o[i];
+                        if (L::ex(i) < 0) store_halo_hi<Q>(fout + i * d.plane + ro, d.nx, o[i]);
                 }
                 if (x == d.nx - 1) {
 #pragma unroll
                     for (int i = 0; i < Q; ++i)
-                        if (L::ex(i) > 0) fout[i * d.plane + ro - 1] = o[i];
+                        if (L::ex(i) > 0) store_halo_lo<Q>(fout + i * d.plane + ro, o[i]);
                 }
             }
         }
@@ -153,7 +153,7 @@ __device__ __forceinline__ void issue_tile_ring(const VDom &d, const float *__re
                                                 int z, int xs, int k, int y0, float *sb, float *ring,
                                                 int rslots, uint64_t *bar) {
     using L = Lat<Q>;
-    constexpr int SEG = TW + 8;
+    constexpr int SEG = TW + 2 * kLead;
     constexpr int NZR = (Q == 9) ? 1 : 3;
     const Nb3 Y = nb3<true>(y, d.ny, d.wall_y);
     Nb3 Z;
@@ -164,7 +164,7 @@ __device__ __forceinline__ void issue_tile_ring(const VDom &d, const float *__re
         Z.wall[0] = Z.wall[1] = Z.wall[2] = false;
     }
     const int nval = min(TW, d.nx - xs);
-    const uint32_t bytes = (uint32_t)((((nval + 3) & ~3) + 8) * 4);
+    const uint32_t bytes = seg_bytes(nval);
     const int jfirst = (k == 0) ? 0 : k + 2;
     mbar_arrive_expect_tx(bar, bytes * (Q + NZR * (k + 3 - jfirst)));
     const uint64_t again = l2_evict_last();
@@ -174,7 +174,7 @@ __device__ __forceinline__ void issue_tile_ring(const VDom &d, const float *__re
         const bool bb = Y.wall[1 - ey] || Z.wall[1 - ez];
         const int si = bb ? L::opp(i) : i;
         const long long ro = bb ? row_offset(d, y, z) : row_offset(d, Y.r[1 - ey], Z.r[1 - ez]);
-        bulk_g2s(sb + i * SEG, fin + si * d.plane + ro + xs - 4, bytes, bar);
+        bulk_g2s(sb + i * SEG, fin + si * d.plane + ro + xs - kLead, bytes, bar);
     }
     for (int j = jfirst; j <= k + 2; ++j) {
         int ry = y0 - 1 + j;                      // y-position y0-1+j, wrapped into [0, ny)
@@ -183,7 +183,7 @@ __device__ __forceinline__ void issue_tile_ring(const VDom &d, const float *__re
 #pragma unroll
         for (int dz = 0; dz < NZR; ++dz) {
             const int rz = (Q == 9) ? 0 : Z.r[dz];
-            bulk_g2s_hint(slot + dz * SEG, d.eps + row_offset(d, ry, rz) + xs - 4, bytes, bar,
+            bulk_g2s_hint(slot + dz * SEG, d.eps + row_offset(d, ry, rz) + xs - kLead, bytes, bar,
                           again);
         }
     }
@@ -193,7 +193,7 @@ __device__ __forceinline__ void issue_tile_ring(const VDom &d, const float *__re
 // V = 4, D3Q19: V = 2), columns x0l..x0l+V-1 of the tile: each population row
 // comes in one or two aligned V-wide shared loads (8 or 16 bytes) and each
 // output row leaves in one V-wide global store.  Segment position p holds
-// column xs - 4 + p.
+// column xs - kLead + p.
 template <int Q, int NT, int V, bool EDGE, bool PL, bool RAG, class Rel>
 __device__ __forceinline__ void ring_tile_vec(const VDom &d, const float *__restrict__ sb,
                                               const float *const ey_slot[3], const Nb3 &Y,
@@ -201,7 +201,7 @@ __device__ __forceinline__ void ring_tile_vec(const VDom &d, const float *__rest
                                               int xs, int tid, Rel &&release) {
     using L = Lat<Q>;
     static_assert(V == 2 || V == 4, "2 or 4 cells per thread");
-    constexpr int SEG = NT * V + 8;
+    constexpr int SEG = NT * V + 2 * kLead;
     constexpr int NZ = (Q == 9) ? 1 : 3;      // z-rows per ring slot
     // plates on nodes (PL instances only): a plate row is written by its
     // fluid neighbour row
@@ -237,19 +237,19 @@ __device__ __forceinline__ void ring_tile_vec(const VDom &d, const float *__rest
         const bool bb = ywall(1 - L::ey(i)) || zwall(1 - L::ez(i));
         const int s = bb ? 0 : -L::ex(i);
         float B[V];
-        vload(row, x0l + 4, B);
+        vload(row, x0l + kLead, B);
         if (s == 0) {
 #pragma unroll
             for (int c = 0; c < V; ++c) h[i][c] = B[c];
         } else if (s < 0) {
             float A[V];
-            vload(row, x0l + 4 - V, A);
+            vload(row, x0l + kLead - V, A);
             h[i][0] = A[V - 1];
 #pragma unroll
             for (int c = 1; c < V; ++c) h[i][c] = B[c - 1];
         } else {
             float C[V];
-            vload(row, x0l + 4 + V, C);
+            vload(row, x0l + kLead + V, C);
 #pragma unroll
             for (int c = 0; c < V - 1; ++c) h[i][c] = B[c + 1];
             h[i][V - 1] = C[0];
@@ -264,14 +264,14 @@ __device__ __forceinline__ void ring_tile_vec(const VDom &d, const float *__rest
         for (int q = 0; q < NZ; ++q) {
             const float *row = ey_slot[r] + q * SEG;
             float B[V];
-            vload(row, x0l + 4, B);
+            vload(row, x0l + kLead, B);
 #pragma unroll
             for (int c = 0; c < V; ++c) E[r][q][c + 1] = B[c];
             const bool side = (Q == 9) || r == 1 || q == 1;
             if (side) {
                 float A[V], C[V];
-                vload(row, x0l + 4 - V, A);
-                vload(row, x0l + 4 + V, C);
+                vload(row, x0l + kLead - V, A);
+                vload(row, x0l + kLead + V, C);
                 E[r][q][0] = A[V - 1];
                 E[r][q][V + 1] = C[0];
             } else {
@@ -315,14 +315,14 @@ __device__ __forceinline__ void ring_tile_vec(const VDom &d, const float *__rest
     if (x0 == 0) {
 #pragma unroll
         for (int i = 0; i < Q; ++i)
-            if (L::ex(i) < 0) fout[i * d.plane + ro + d.nx] = out[i][0];
+            if (L::ex(i) < 0) store_halo_hi<Q>(fout + i * d.plane + ro, d.nx, out[i][0]);
     }
 #pragma unroll
     for (int c = 0; c < V; ++c) {
         if (x0 + c == d.nx - 1) {
 #pragma unroll
             for (int i = 0; i < Q; ++i)
-                if (L::ex(i) > 0) fout[i * d.plane + ro - 1] = out[i][c];
+                if (L::ex(i) > 0) store_halo_lo<Q>(fout + i * d.plane + ro, out[i][c]);
         }
     }
     if (plo || phi) store_plates<Q, V>(d, fout, y, z, x0, plo, phi, lo, hi);
@@ -344,7 +344,7 @@ __device__ __forceinline__ void ring_tile(const VDom &d, const float *__restrict
                                           float *__restrict__ fout, int y, int z, int xs, int tid,
                                           Rel &&release) {
     using L = Lat<Q>;
-    constexpr int SEG = NT * CPT + 8;
+    constexpr int SEG = NT * CPT + 2 * kLead;
     if constexpr (VEC) {
         ring_tile_vec<Q, NT, CPT, EDGE, PL, RAG>(d, sb, ey_slot, Y, Z, fout, y, z, xs, tid, release);
     } else {
@@ -366,16 +366,16 @@ __device__ __forceinline__ void ring_tile(const VDom &d, const float *__restrict
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 const bool bb = ywall(1 - L::ey(i)) || zwall(1 - L::ez(i));
-                h[cc][i] = sb[i * SEG + 4 + xl + (bb ? 0 : -L::ex(i))];
+                h[cc][i] = sb[i * SEG + kLead + xl + (bb ? 0 : -L::ex(i))];
             }
-            const float e0 = ey_slot[1][(Q == 9 ? 0 : 1) * SEG + 4 + xl];
+            const float e0 = ey_slot[1][(Q == 9 ? 0 : 1) * SEG + kLead + xl];
             et[cc][0] = e0;
 #pragma unroll
             for (int i = 1; i < Q; ++i) {
                 const int ey = L::ey(i), ez = L::ez(i);
                 const bool wall = ywall(1 + ey) || zwall(1 + ez);
                 et[cc][i] =
-                    wall ? e0 : ey_slot[1 + ey][(Q == 9 ? 0 : 1 + ez) * SEG + 4 + xl + L::ex(i)];
+                    wall ? e0 : ey_slot[1 + ey][(Q == 9 ? 0 : 1 + ez) * SEG + kLead + xl + L::ex(i)];
             }
         }
         release();
@@ -414,12 +414,12 @@ __device__ __forceinline__ void ring_tile(const VDom &d, const float *__restrict
                 if (x == 0) {
 #pragma unroll
                     for (int i = 0; i < Q; ++i)
-                        if (L::ex(i) < 0) fout[i * d.plane + ro + d.nx] = o[i];
+                        if (L::ex(i) < 0) store_halo_hi<Q>(fout + i * d.plane + ro, d.nx, o[i]);
                 }
                 if (x == d.nx - 1) {
 #pragma unroll
                     for (int i = 0; i < Q; ++i)
-                        if (L::ex(i) > 0) fout[i * d.plane + ro - 1] = o[i];
+                        if (L::ex(i) > 0) store_halo_lo<Q>(fout + i * d.plane + ro, o[i]);
                 }
             }
         }
@@ -446,7 +446,7 @@ __device__ __forceinline__ void ring_strip(const VDom &d, const float *__restric
                                            float *__restrict__ fout, int xs, int z, int y0, int y1,
                                            int stages, unsigned char *smem) {
     constexpr int TW = NT * CPT;
-    constexpr int SEG = TW + 8;
+    constexpr int SEG = TW + 2 * kLead;
     constexpr int NZR = (Q == 9) ? 1 : 3;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
     float *buf = reinterpret_cast<float *>(smem + kBarBytes);
@@ -524,7 +524,7 @@ __device__ __forceinline__ void ring_strip_ws(const VDom &d, const float *__rest
                                               float *__restrict__ fout, int xs, int z, int y0, int y1,
                                               int stages, unsigned char *smem) {
     constexpr int TW = NT * CPT;
-    constexpr int SEG = TW + 8;
+    constexpr int SEG = TW + 2 * kLead;
     constexpr int NZR = (Q == 9) ? 1 : 3;
     constexpr int NCW = NT / 32;          // compute warps
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
@@ -682,7 +682,7 @@ template <int Q, int NT, int CPT, bool VEC, bool PL, bool RAG, class Cur>
 __device__ __forceinline__ void ilv_run(Cur cur, const int *status, int ntiles, int stages,
                                         unsigned char *smem) {
     constexpr int TW = NT * CPT;
-    constexpr int SEG = TW + 8;
+    constexpr int SEG = TW + 2 * kLead;
     constexpr int NS = Q + EpsRows<Q>::N;
     constexpr int NZR = (Q == 9) ? 1 : 3;
     constexpr int NCW = NT / 32;
@@ -783,20 +783,38 @@ __global__ void __launch_bounds__(NT + 32) k_step_ilv_batched(const VDom *__rest
         stages, smem);
 }
 
+// Dynamic shared memory to request for a kernel that needs `need` bytes so
+// that at most `ctas` of its CTAs fit on one SM (0: as many as fit).  Fewer
+// CTAs mean fewer row segments in flight: past a point, more outstanding
+// copies of the 19 (or 9) direction planes lower the DRAM throughput.
+static size_t cap_smem(size_t need, int ctas) {
+    if (ctas <= 0) return need;
+    int dev = 0, per_sm = 0, reserved = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    // just too large for ctas + 1 CTAs per SM, small enough for ctas
+    size_t share = (size_t)(per_sm / (ctas + 1) - reserved + 128) & ~(size_t)127;
+    if (share > (size_t)optin) share = (size_t)optin;
+    return need > share ? need : share;
+}
+
 template <int Q, int NT, int CPT, bool VEC, bool PL = false>
-static cudaError_t launch_ilv_t(const VDom &d, const float *fin, float *fout, int stages,
+static cudaError_t launch_ilv_t(const VDom &d, const float *fin, float *fout, int stages, int ctas,
                                 cudaStream_t stream) {
     constexpr int TW = NT * CPT;
     constexpr int NS = Q + EpsRows<Q>::N;
-    const size_t smem = kBarBytes + (size_t)stages * NS * (TW + 8) * sizeof(float);
+    const size_t smem = kBarBytes + (size_t)stages * NS * (TW + 2 * kLead) * sizeof(float);
     if (stages < 2 || stages > kBarBytes / 16 || smem > 227 * 1024) return cudaErrorInvalidValue;
+    const size_t smem_req = cap_smem(smem, ctas);
     auto kern = k_step_tma_ilv<Q, NT, CPT, VEC, PL>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_req);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, occ = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT + 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT + 32, smem_req);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     const int ntx = (d.nx + TW - 1) / TW;
@@ -804,7 +822,7 @@ static cudaError_t launch_ilv_t(const VDom &d, const float *fin, float *fout, in
     if (ntiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     long long grid = (long long)sms * occ;
     if (grid > ntiles) grid = ntiles;
-    kern<<<(unsigned)grid, NT + 32, smem, stream>>>(d, fin, fout, ntx, (int)ntiles, stages);
+    kern<<<(unsigned)grid, NT + 32, smem_req, stream>>>(d, fin, fout, ntx, (int)ntiles, stages);
     return cudaGetLastError();
 }
 
@@ -845,22 +863,23 @@ static int pick_per_y(int ncol, int ny, long long resident) {
 }
 
 template <int Q, int NT, int CPT, bool VEC = false, bool WS = false, bool PL = false>
-static cudaError_t launch_ring_t(const VDom &d, const float *fin, float *fout, int stages,
+static cudaError_t launch_ring_t(const VDom &d, const float *fin, float *fout, int stages, int ctas,
                                  cudaStream_t stream) {
     constexpr int TW = NT * CPT;
     constexpr int NZR = (Q == 9) ? 1 : 3;
     const size_t smem =
-        kBarBytes + (size_t)(stages * Q + (stages + 2) * NZR) * (TW + 8) * sizeof(float);
+        kBarBytes + (size_t)(stages * Q + (stages + 2) * NZR) * (TW + 2 * kLead) * sizeof(float);
     const int max_stages = WS ? kBarBytes / 16 : kBarBytes / 8;
     if (stages < 2 || stages > max_stages || smem > 227 * 1024) return cudaErrorInvalidValue;
+    const size_t smem_req = cap_smem(smem, ctas);
     auto kern = k_step_tma_ring<Q, NT, CPT, VEC, WS, PL>;
     constexpr int nthreads = WS ? NT + 32 : NT;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_req);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, occ = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, nthreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, nthreads, smem_req);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     const int ntx = (d.nx + TW - 1) / TW;
@@ -868,7 +887,7 @@ static cudaError_t launch_ring_t(const VDom &d, const float *fin, float *fout, i
     const int per_y = pick_per_y(ncol, d.ny, (long long)sms * occ);
     const long long grid = (long long)ncol * per_y;
     if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    kern<<<(unsigned)grid, nthreads, smem, stream>>>(d, fin, fout, ntx, per_y, stages);
+    kern<<<(unsigned)grid, nthreads, smem_req, stream>>>(d, fin, fout, ntx, per_y, stages);
     return cudaGetLastError();
 }
 
@@ -876,22 +895,23 @@ template <int Q, int NT, int CPT>
 static size_t tma_smem_bytes(int stages) {
     constexpr int TW = NT * CPT;
     constexpr int NS = Q + EpsRows<Q>::N;
-    return kBarBytes + (size_t)stages * NS * (TW + 8) * sizeof(float);
+    return kBarBytes + (size_t)stages * NS * (TW + 2 * kLead) * sizeof(float);
 }
 
 template <int Q, int NT, int CPT>
-static cudaError_t launch_tma_t(const VDom &d, const float *fin, float *fout, int stages,
+static cudaError_t launch_tma_t(const VDom &d, const float *fin, float *fout, int stages, int ctas,
                                 cudaStream_t stream) {
     constexpr int TW = NT * CPT;
     const size_t smem = tma_smem_bytes<Q, NT, CPT>(stages);
     if (stages < 2 || stages > 16 || smem > 227 * 1024) return cudaErrorInvalidValue;
+    const size_t smem_req = cap_smem(smem, ctas);
     auto kern = k_step_tma<Q, NT, CPT>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_req);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, occ = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem_req);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     const int ntx = (d.nx + TW - 1) / TW;
@@ -899,44 +919,46 @@ static cudaError_t launch_tma_t(const VDom &d, const float *fin, float *fout, in
     if (ntiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     long long grid = (long long)sms * occ;
     if (grid > ntiles) grid = ntiles;
-    kern<<<(unsigned)grid, NT, smem, stream>>>(d, fin, fout, ntx, (int)ntiles, stages);
+    kern<<<(unsigned)grid, NT, smem_req, stream>>>(d, fin, fout, ntx, (int)ntiles, stages);
     return cudaGetLastError();
 }
 
 template <int NT, int CPT, bool VEC = false, bool WS = false>
 static cudaError_t launch_ring_batched_t(const VDom *doms, const Tile *strips, int nstrips, int parity,
-                                         int stages, cudaStream_t stream) {
+                                         int stages, int ctas, cudaStream_t stream) {
     constexpr int TW = NT * CPT;
-    const size_t smem = kBarBytes + (size_t)(stages * 9 + (stages + 2)) * (TW + 8) * sizeof(float);
+    const size_t smem = kBarBytes + (size_t)(stages * 9 + (stages + 2)) * (TW + 2 * kLead) * sizeof(float);
     const int max_stages = WS ? kBarBytes / 16 : kBarBytes / 8;
     if (stages < 2 || stages > max_stages || smem > 227 * 1024 || nstrips < 1)
         return cudaErrorInvalidValue;
+    const size_t smem_req = cap_smem(smem, ctas);
     auto kern = k_step_ring_batched<NT, CPT, VEC, WS>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_req);
     if (e != cudaSuccess) return e;
-    kern<<<nstrips, WS ? NT + 32 : NT, smem, stream>>>(doms, strips, parity, stages);
+    kern<<<nstrips, WS ? NT + 32 : NT, smem_req, stream>>>(doms, strips, parity, stages);
     return cudaGetLastError();
 }
 
 template <int NT, int CPT, bool VEC>
 static cudaError_t launch_ilv_batched_t(const VDom *doms, const Tile *tiles, int ntiles, int parity,
-                                        int stages, int *status, cudaStream_t stream) {
+                                        int stages, int ctas, int *status, cudaStream_t stream) {
     constexpr int TW = NT * CPT;
-    const size_t smem = kBarBytes + (size_t)stages * 12 * (TW + 8) * sizeof(float);
+    const size_t smem = kBarBytes + (size_t)stages * 12 * (TW + 2 * kLead) * sizeof(float);
     if (stages < 2 || stages > kBarBytes / 16 || smem > 227 * 1024 || ntiles < 1)
         return cudaErrorInvalidValue;
+    const size_t smem_req = cap_smem(smem, ctas);
     auto kern = k_step_ilv_batched<NT, CPT, VEC>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_req);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, occ = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT + 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT + 32, smem_req);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     long long grid = (long long)sms * occ;
     if (grid > ntiles) grid = ntiles;
-    kern<<<(unsigned)grid, NT + 32, smem, stream>>>(doms, tiles, ntiles, parity, stages, status);
+    kern<<<(unsigned)grid, NT + 32, smem_req, stream>>>(doms, tiles, ntiles, parity, stages, status);
     return cudaGetLastError();
 }
 
@@ -948,32 +970,32 @@ cudaError_t launch_ring_batched(const VDom *doms, const Tile *strips, int nstrip
     const int st = L.rows;
     if (L.kind == 6) {     // interleaved tile table, strided cells
         if (nt == 128 && L.cpt == 2)
-            return launch_ilv_batched_t<128, 2, false>(doms, strips, nstrips, parity, st, status, stream);
+            return launch_ilv_batched_t<128, 2, false>(doms, strips, nstrips, parity, st, L.ctas, status, stream);
         if (nt == 256 && L.cpt == 2)
-            return launch_ilv_batched_t<256, 2, false>(doms, strips, nstrips, parity, st, status, stream);
+            return launch_ilv_batched_t<256, 2, false>(doms, strips, nstrips, parity, st, L.ctas, status, stream);
         return cudaErrorInvalidValue;
     }
     if (L.kind == 7) {     // interleaved tile table, 4 consecutive cells
         if (nt == 64 && L.cpt == 4)
-            return launch_ilv_batched_t<64, 4, true>(doms, strips, nstrips, parity, st, status, stream);
+            return launch_ilv_batched_t<64, 4, true>(doms, strips, nstrips, parity, st, L.ctas, status, stream);
         if (nt == 128 && L.cpt == 4)
-            return launch_ilv_batched_t<128, 4, true>(doms, strips, nstrips, parity, st, status, stream);
+            return launch_ilv_batched_t<128, 4, true>(doms, strips, nstrips, parity, st, L.ctas, status, stream);
         return cudaErrorInvalidValue;
     }
     if (L.kind == 5) {
         if (nt == 64 && L.cpt == 4)
-            return launch_ring_batched_t<64, 4, true, true>(doms, strips, nstrips, parity, st, stream);
+            return launch_ring_batched_t<64, 4, true, true>(doms, strips, nstrips, parity, st, L.ctas, stream);
         if (nt == 128 && L.cpt == 4)
-            return launch_ring_batched_t<128, 4, true, true>(doms, strips, nstrips, parity, st, stream);
+            return launch_ring_batched_t<128, 4, true, true>(doms, strips, nstrips, parity, st, L.ctas, stream);
         return cudaErrorInvalidValue;
     }
     if (L.kind != 2 && L.kind != 4) return cudaErrorInvalidValue;
     const bool ws = L.kind == 4;
 #define VANS_RB_CASE(NTT, CC)                                                                   \
     if (nt == NTT && L.cpt == CC)                                                               \
-        return ws ? launch_ring_batched_t<NTT, CC, false, true>(doms, strips, nstrips, parity, st, \
+        return ws ? launch_ring_batched_t<NTT, CC, false, true>(doms, strips, nstrips, parity, st, L.ctas, \
                                                                stream)                        \
-                  : launch_ring_batched_t<NTT, CC>(doms, strips, nstrips, parity, st, stream);
+                  : launch_ring_batched_t<NTT, CC>(doms, strips, nstrips, parity, st, L.ctas, stream);
     VANS_RB_CASE(128, 2)
     VANS_RB_CASE(128, 4)
     VANS_RB_CASE(256, 1)
@@ -1005,18 +1027,18 @@ static cudaError_t launch_plates(int q, const VDom &d, const float *fin, float *
     if (!plate_shape(q, L)) return cudaErrorInvalidValue;
     if (q == 9) {
         if (L.kind == 2)
-            return L.cpt == 2 ? launch_ring_t<9, 128, 2, false, false, true>(d, fin, fout, st, stream)
-                              : launch_ring_t<9, 128, 4, false, false, true>(d, fin, fout, st, stream);
+            return L.cpt == 2 ? launch_ring_t<9, 128, 2, false, false, true>(d, fin, fout, st, L.ctas, stream)
+                              : launch_ring_t<9, 128, 4, false, false, true>(d, fin, fout, st, L.ctas, stream);
         if (L.kind == 5)
-            return nt == 64 ? launch_ring_t<9, 64, 4, true, true, true>(d, fin, fout, st, stream)
-                            : launch_ring_t<9, 128, 4, true, true, true>(d, fin, fout, st, stream);
-        return nt == 64 ? launch_ilv_t<9, 64, 4, true, true>(d, fin, fout, st, stream)
-                        : launch_ilv_t<9, 128, 4, true, true>(d, fin, fout, st, stream);
+            return nt == 64 ? launch_ring_t<9, 64, 4, true, true, true>(d, fin, fout, st, L.ctas, stream)
+                            : launch_ring_t<9, 128, 4, true, true, true>(d, fin, fout, st, L.ctas, stream);
+        return nt == 64 ? launch_ilv_t<9, 64, 4, true, true>(d, fin, fout, st, L.ctas, stream)
+                        : launch_ilv_t<9, 128, 4, true, true>(d, fin, fout, st, L.ctas, stream);
     }
-    if (L.kind == 2) return launch_ring_t<19, 128, 1, false, false, true>(d, fin, fout, st, stream);
-    if (L.kind == 3) return launch_ring_t<19, 128, 2, true, false, true>(d, fin, fout, st, stream);
-    if (L.kind == 5) return launch_ring_t<19, 128, 2, true, true, true>(d, fin, fout, st, stream);
-    return launch_ilv_t<19, 128, 2, true, true>(d, fin, fout, st, stream);
+    if (L.kind == 2) return launch_ring_t<19, 128, 1, false, false, true>(d, fin, fout, st, L.ctas, stream);
+    if (L.kind == 3) return launch_ring_t<19, 128, 2, true, false, true>(d, fin, fout, st, L.ctas, stream);
+    if (L.kind == 5) return launch_ring_t<19, 128, 2, true, true, true>(d, fin, fout, st, L.ctas, stream);
+    return launch_ilv_t<19, 128, 2, true, true>(d, fin, fout, st, L.ctas, stream);
 }
 
 cudaError_t launch_step_tma(int q, const VDom &d, const float *fin, float *fout, Launch L,
@@ -1024,17 +1046,17 @@ cudaError_t launch_step_tma(int q, const VDom &d, const float *fin, float *fout,
     if (d.nee) return launch_plates(q, d, fin, fout, L, stream);
     const int nt = 32 * L.warps;
     if (L.kind == 6) {                  // interleaved tiles, strided cells per thread
-        if (q == 9 && nt == 128 && L.cpt == 2) return launch_ilv_t<9, 128, 2, false>(d, fin, fout, L.rows, stream);
-        if (q == 9 && nt == 256 && L.cpt == 2) return launch_ilv_t<9, 256, 2, false>(d, fin, fout, L.rows, stream);
-        if (q == 19 && nt == 128 && L.cpt == 1) return launch_ilv_t<19, 128, 1, false>(d, fin, fout, L.rows, stream);
-        if (q == 19 && nt == 256 && L.cpt == 1) return launch_ilv_t<19, 256, 1, false>(d, fin, fout, L.rows, stream);
+        if (q == 9 && nt == 128 && L.cpt == 2) return launch_ilv_t<9, 128, 2, false>(d, fin, fout, L.rows, L.ctas, stream);
+        if (q == 9 && nt == 256 && L.cpt == 2) return launch_ilv_t<9, 256, 2, false>(d, fin, fout, L.rows, L.ctas, stream);
+        if (q == 19 && nt == 128 && L.cpt == 1) return launch_ilv_t<19, 128, 1, false>(d, fin, fout, L.rows, L.ctas, stream);
+        if (q == 19 && nt == 256 && L.cpt == 1) return launch_ilv_t<19, 256, 1, false>(d, fin, fout, L.rows, L.ctas, stream);
         return cudaErrorInvalidValue;
     }
     if (L.kind == 7) {                  // interleaved tiles, consecutive cells per thread
-        if (q == 9 && nt == 64 && L.cpt == 4) return launch_ilv_t<9, 64, 4, true>(d, fin, fout, L.rows, stream);
-        if (q == 9 && nt == 128 && L.cpt == 4) return launch_ilv_t<9, 128, 4, true>(d, fin, fout, L.rows, stream);
-        if (q == 19 && nt == 64 && L.cpt == 2) return launch_ilv_t<19, 64, 2, true>(d, fin, fout, L.rows, stream);
-        if (q == 19 && nt == 128 && L.cpt == 2) return launch_ilv_t<19, 128, 2, true>(d, fin, fout, L.rows, stream);
+        if (q == 9 && nt == 64 && L.cpt == 4) return launch_ilv_t<9, 64, 4, true>(d, fin, fout, L.rows, L.ctas, stream);
+        if (q == 9 && nt == 128 && L.cpt == 4) return launch_ilv_t<9, 128, 4, true>(d, fin, fout, L.rows, L.ctas, stream);
+        if (q == 19 && nt == 64 && L.cpt == 2) return launch_ilv_t<19, 64, 2, true>(d, fin, fout, L.rows, L.ctas, stream);
+        if (q == 19 && nt == 128 && L.cpt == 2) return launch_ilv_t<19, 128, 2, true>(d, fin, fout, L.rows, L.ctas, stream);
         return cudaErrorInvalidValue;
     }
     if (L.kind == 3 || L.kind == 5) {   // ring pipeline, consecutive cells per thread
@@ -1042,28 +1064,28 @@ cudaError_t launch_step_tma(int q, const VDom &d, const float *fin, float *fout,
         if (q == 19) {                  // 2 cells per thread
             if (L.cpt != 2) return cudaErrorInvalidValue;
             if (nt == 64)
-                return ws ? launch_ring_t<19, 64, 2, true, true>(d, fin, fout, L.rows, stream)
-                          : launch_ring_t<19, 64, 2, true>(d, fin, fout, L.rows, stream);
+                return ws ? launch_ring_t<19, 64, 2, true, true>(d, fin, fout, L.rows, L.ctas, stream)
+                          : launch_ring_t<19, 64, 2, true>(d, fin, fout, L.rows, L.ctas, stream);
             if (nt == 128)
-                return ws ? launch_ring_t<19, 128, 2, true, true>(d, fin, fout, L.rows, stream)
-                          : launch_ring_t<19, 128, 2, true>(d, fin, fout, L.rows, stream);
+                return ws ? launch_ring_t<19, 128, 2, true, true>(d, fin, fout, L.rows, L.ctas, stream)
+                          : launch_ring_t<19, 128, 2, true>(d, fin, fout, L.rows, L.ctas, stream);
             return cudaErrorInvalidValue;
         }
         if (q != 9 || L.cpt != 4) return cudaErrorInvalidValue;
         if (nt == 64)
-            return ws ? launch_ring_t<9, 64, 4, true, true>(d, fin, fout, L.rows, stream)
-                      : launch_ring_t<9, 64, 4, true>(d, fin, fout, L.rows, stream);
+            return ws ? launch_ring_t<9, 64, 4, true, true>(d, fin, fout, L.rows, L.ctas, stream)
+                      : launch_ring_t<9, 64, 4, true>(d, fin, fout, L.rows, L.ctas, stream);
         if (nt == 128)
-            return ws ? launch_ring_t<9, 128, 4, true, true>(d, fin, fout, L.rows, stream)
-                      : launch_ring_t<9, 128, 4, true>(d, fin, fout, L.rows, stream);
+            return ws ? launch_ring_t<9, 128, 4, true, true>(d, fin, fout, L.rows, L.ctas, stream)
+                      : launch_ring_t<9, 128, 4, true>(d, fin, fout, L.rows, L.ctas, stream);
         return cudaErrorInvalidValue;
     }
     if (L.kind == 2 || L.kind == 4) {
         const bool ws = L.kind == 4;
 #define VANS_RING_CASE(QQ, NTT, CC)                                                     \
         if (q == QQ && nt == NTT && L.cpt == CC)                                        \
-            return ws ? launch_ring_t<QQ, NTT, CC, false, true>(d, fin, fout, L.rows, stream) \
-                      : launch_ring_t<QQ, NTT, CC>(d, fin, fout, L.rows, stream);
+            return ws ? launch_ring_t<QQ, NTT, CC, false, true>(d, fin, fout, L.rows, L.ctas, stream) \
+                      : launch_ring_t<QQ, NTT, CC>(d, fin, fout, L.rows, L.ctas, stream);
         VANS_RING_CASE(9, 128, 2)
         VANS_RING_CASE(9, 128, 4)
         VANS_RING_CASE(9, 256, 1)
@@ -1076,7 +1098,7 @@ cudaError_t launch_step_tma(int q, const VDom &d, const float *fin, float *fout,
     }
 #define VANS_TMA_CASE(QQ, NTT, CC)                              \
     if (q == QQ && nt == NTT && L.cpt == CC)                    \
-        return launch_tma_t<QQ, NTT, CC>(d, fin, fout, L.rows, stream);
+        return launch_tma_t<QQ, NTT, CC>(d, fin, fout, L.rows, L.ctas, stream);
     VANS_TMA_CASE(9, 128, 2)
     VANS_TMA_CASE(9, 128, 4)
     VANS_TMA_CASE(9, 256, 1)

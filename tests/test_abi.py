@@ -51,7 +51,7 @@ def _sizes(lib, **kw):
 
 def test_size_queries(lib):
     sf, wb = _sizes(lib, q=9, nx=4096, ny=4096, tau=0.6)
-    pitch = 4128                       # 4 + round_up(4096, 128) + 1, rounded up to 32
+    pitch = 4128                       # 8 + round_up(4096, 128) + 1, rounded up to 32
     assert sf == 9 * 4096 * pitch
     assert wb == (2 * sf + 4096 * pitch + 64) * 4
     sf3, _ = _sizes(lib, q=19, nx=256, ny=256, nz=256, tau=0.6, wall_mask=6)

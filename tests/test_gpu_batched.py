@@ -42,7 +42,8 @@ def test_batched_matches_oracle_per_domain():
                                Launch(4, 4, 3, 2), Launch(2, 8, 2, 2), Launch(1, 8, 3, 2),
                                Launch(2, 8, 2, 4), Launch(1, 8, 3, 4), Launch(4, 4, 4, 5),
                                Launch(4, 2, 2, 5), Launch(2, 4, 2, 6), Launch(2, 8, 3, 6),
-                               Launch(4, 4, 4, 7), Launch(4, 2, 3, 7)])
+                               Launch(4, 4, 4, 7), Launch(4, 2, 3, 7), Launch(4, 4, 2, 7, 2),
+                               Launch(4, 4, 2, 5, 2)])
 def test_batched_launch_shapes(L):
     torch = torch_cuda()
     doms = W.batched_channels(n=4, seed=43, nx_range=(20, 300), ny_range=(4, 40))

@@ -25,7 +25,8 @@ STEP_CASES = [
                          Launch(2, 4, 3, 1), Launch(1, 8, 2, 1), Launch(2, 4, 3, 2),
                          Launch(4, 4, 3, 3), Launch(4, 2, 2, 3), Launch(2, 4, 3, 4),
                          Launch(4, 4, 3, 5), Launch(4, 2, 2, 5), Launch(2, 4, 2, 6),
-                         Launch(2, 8, 3, 6), Launch(4, 4, 2, 7), Launch(4, 2, 3, 7)]),
+                         Launch(2, 8, 3, 6), Launch(4, 4, 2, 7), Launch(4, 2, 3, 7),
+                         Launch(4, 4, 2, 7, 2), Launch(4, 4, 3, 5, 1), Launch(2, 4, 3, 2, 3)]),
     (9, (1, 6, 5), 0, [Launch(4, 2, 1), Launch(1, 2, 1), Launch(4, 4, 2, 1), Launch(1, 8, 2, 2),
                        Launch(4, 2, 3, 3)]),
     (9, (1, 1, 1), 0, [Launch(4, 2, 1), Launch(2, 4, 3, 1), Launch(2, 4, 3, 2), Launch(4, 4, 3, 3),
@@ -43,7 +44,8 @@ STEP_CASES = [
                          Launch(2, 4, 2, 1), Launch(1, 4, 3, 2), Launch(2, 4, 2, 2),
                          Launch(1, 4, 3, 4), Launch(2, 4, 2, 4), Launch(2, 4, 3, 3),
                          Launch(2, 4, 2, 5), Launch(2, 2, 4, 5), Launch(1, 4, 2, 6),
-                         Launch(1, 8, 3, 6), Launch(2, 4, 2, 7), Launch(2, 2, 3, 7)]),
+                         Launch(1, 8, 3, 6), Launch(2, 4, 2, 7), Launch(2, 2, 3, 7),
+                         Launch(2, 4, 2, 7, 1), Launch(2, 4, 2, 3, 2), Launch(1, 4, 3, 1, 2)]),
     (19, (5, 4, 33), 2, [Launch(2, 2, 1), Launch(1, 8, 3, 1), Launch(1, 8, 2, 2), Launch(2, 2, 3, 3),
                          Launch(2, 4, 4, 5)]),
     (19, (3, 3, 4), 0, [Launch(1, 2, 1), Launch(1, 4, 4, 1), Launch(1, 4, 4, 2)]),
@@ -51,7 +53,7 @@ STEP_CASES = [
                         Launch(1, 4, 2, 6), Launch(2, 4, 2, 7)]),
     (19, (6, 30, 300), 4, [Launch(2, 4, 3, 2), Launch(1, 8, 3, 2), Launch(1, 8, 3, 4),
                            Launch(2, 4, 3, 5), Launch(2, 2, 2, 3), Launch(1, 8, 2, 6),
-                           Launch(2, 4, 3, 7)]),
+                           Launch(2, 4, 3, 7), Launch(2, 4, 2, 7, 2)]),
 ]
 
 
@@ -351,3 +353,18 @@ def test_monitored_steps_emit_the_moments_and_reductions():
     b.set_populations(f)
     _, _, st = b.step_monitored(1, 1, rho, u)
     assert st[2].item() == 1.0
+
+
+def test_cta_cap_refusals_and_roundtrip():
+    """ctas (CTAs per SM) is taken by the pipelined kinds only, within 1..4;
+    the reverse step takes none; a capped shape reads back unchanged."""
+    torch_cuda()
+    p, eps, _ = W.periodic_2d_shape(64, 16, nsteps=0)
+    s = solver(p, eps)
+    for L in (Launch(4, 4, 1, 0, 1), Launch(4, 4, 2, 7, 5), Launch(4, 4, 2, 7, -1)):
+        with pytest.raises(VansError):
+            s.launch = L
+    with pytest.raises(VansError):
+        s.set_adjoint_launch(Launch(1, 4, 4, 1, 2))
+    s.launch = Launch(4, 4, 2, 7, 2)
+    assert s.launch == Launch(4, 4, 2, 7, 2)
