@@ -35,6 +35,7 @@ PLATE_CASES = [
      [Launch(1, 2, 1), Launch(2, 2, 2), Launch(1, 4, 3, 2), Launch(2, 4, 2, 3),
       Launch(2, 4, 3, 5), Launch(2, 4, 2, 7)]),
     (19, (6, 30, 300), (0.0, 0.0, 0.0), [Launch(1, 4, 3, 2), Launch(2, 4, 3, 7)]),
+    (19, (5, 8, 64), (0.01, 0.0, 0.0), [Launch(2, 4, 2, 7), Launch(2, 4, 3, 7)]),
 ]
 
 

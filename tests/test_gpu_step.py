@@ -54,6 +54,15 @@ STEP_CASES = [
     (19, (6, 30, 300), 4, [Launch(2, 4, 3, 2), Launch(1, 8, 3, 2), Launch(1, 8, 3, 4),
                            Launch(2, 4, 3, 5), Launch(2, 2, 2, 3), Launch(1, 8, 2, 6),
                            Launch(2, 4, 3, 7), Launch(2, 4, 2, 7, 2)]),
+    # D3Q19 rows of a multiple of 8 cells, each row one tile (or two): the
+    # halo columns sit in sectors of their own
+    (19, (4, 6, 64), 0, [Launch(2, 4, 2, 7), Launch(2, 2, 2, 7), Launch(2, 4, 3, 7, 2),
+                         Launch(1, 4, 2, 6), Launch(1, 8, 3, 6), Launch(2, 4, 2, 3)]),
+    (19, (3, 5, 128), 6, [Launch(2, 2, 2, 7), Launch(1, 4, 2, 6), Launch(2, 4, 2, 7),
+                          Launch(1, 8, 2, 6)]),
+    (19, (2, 4, 256), 2, [Launch(2, 4, 2, 7), Launch(2, 2, 3, 7), Launch(1, 8, 2, 6),
+                          Launch(1, 4, 3, 6)]),
+    (19, (2, 3, 8), 6, [Launch(2, 4, 2, 7), Launch(1, 4, 2, 6)]),
 ]
 
 
@@ -259,6 +268,8 @@ MOVING = [
       Launch(1, 4, 2, 6), Launch(2, 4, 2, 7)]),
     (19, (4, 5, 9), 2, (0.0, 0.0, 0.01), [Launch(2, 2, 1), Launch(1, 8, 2, 2), Launch(1, 8, 2, 4),
                                           Launch(2, 4, 2, 5)]),
+    (19, (5, 7, 64), 6, (0.01, 0.0, 0.004), [Launch(2, 4, 2, 7), Launch(1, 4, 2, 6),
+                                             Launch(2, 2, 2, 7)]),
 ]
 
 
