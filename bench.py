@@ -38,6 +38,9 @@ METRIC = "MLUPS and % of HBM-bandwidth roofline; batched and adjoint MLUPS vs pl
 WORKLOAD = ("D2Q9 4096x4096 periodic, eps smoothed noise (sigma 16) in [0.4,1.0], tau 0.6, "
             "Ergun drag (d_p 21.33) + Forchheimer, body force along x, FP32 populations")
 BYTES_PER_CELL = {9: 9 * 4 * 2 + 4, 19: 19 * 4 * 2 + 4}     # algorithmic bytes per update
+# reverse step, D2Q9: lambda in and out (72), the state it reads (36), eps (4),
+# the compensated eps-gradient accumulators read and written (2 x 24)
+ADJ_BYTES_PER_CELL = 9 * 4 * 2 + 9 * 4 + 4 + 2 * 24
 FALLBACK_HBM_GBS = 6800.0
 
 # DRAM bytes per launch of the step kernel measured by ncu on the 4096^2
@@ -354,6 +357,37 @@ def bench_adjoint(torch, V, W, args=None):
         s.close()
     out["note"] = ("value: all-FP32 reverse step; fp64_arith: per-cell reverse arithmetic in FP64; "
                    "fd_err_*: max over 32 cells of |dJ/deps - FP64 FD| / max |FD|")
+    if args is None or args.only != "adjoint":
+        out["kernel_4096"] = bench_adjoint_kernel(torch, V, W)
+    return out
+
+
+def bench_adjoint_kernel(torch, V, W, n=4096, steps=40):
+    """The reverse step alone on the plain step's 4096^2 workload (its buffers
+    far exceed L2): K calls of vans_step_adjoint, lambda ping-ponged, timed
+    with CUDA events on the solver's stream."""
+    p, eps, _ = W.periodic_2d(n)
+    cells = p["nx"] * p["ny"]
+    s = V.Solver(p)
+    s.set_eps(torch.from_numpy(eps).cuda().view(-1))
+    s.step(50)
+    state = s.get_state()
+    lam = [s.new_state(), s.new_state()]
+    grad = torch.zeros(s.grad_floats(), dtype=torch.float32, device="cuda")
+    s.flux_seed(p["nx"] - 1, lam[0], grad, state)
+    for k in range(3):
+        s.step_adjoint(state, lam[k % 2], lam[(k + 1) % 2], grad)
+    t = time_region(torch, s.stream,
+                    lambda: [s.step_adjoint(state, lam[k % 2], lam[(k + 1) % 2], grad)
+                             for k in range(steps)])
+    out = {"workload": f"D2Q9 {n}x{n} periodic (the plain step's), reverse step alone",
+           "steps": steps, "value": cells * steps / t / 1e6, "unit": "MLUPS",
+           "bytes_per_cell": ADJ_BYTES_PER_CELL,
+           "gb_s": ADJ_BYTES_PER_CELL * cells * steps / t / 1e9,
+           "launch": "default reverse launch (kind 1: 1 cell per thread, 4 compute warps, 4 stages)",
+           "finite": bool(torch.isfinite(grad).all().item())}
+    out["frac_of_peak"] = out["gb_s"] / peaks()[0]
+    s.close()
     return out
 
 

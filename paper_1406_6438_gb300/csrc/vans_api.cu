@@ -373,7 +373,8 @@ std::vector<Launch> candidates(int q, bool batched) {
                             {1, 8, 3, 2}, {2, 8, 2, 4}, {2, 4, 2, 4}, {4, 2, 2, 5}, {4, 2, 3, 5},
                             {4, 4, 2, 5}, {4, 4, 3, 5}, {4, 4, 4, 5}, {2, 4, 2, 6}, {2, 8, 2, 6},
                             {4, 2, 4, 7}, {4, 2, 3, 7}, {4, 4, 2, 7}, {4, 4, 4, 7},
-                            {4, 4, 2, 5, 2}, {4, 4, 2, 7, 2}, {4, 4, 3, 7, 2}};
+                            {4, 4, 2, 5, 2}, {4, 4, 2, 7, 2}, {4, 4, 3, 7, 2},
+                            {2, 4, 2, 2}, {2, 4, 4, 2}, {2, 4, 3, 4}};
         c.insert(c.end(), std::begin(t), std::end(t));
         return c;
     }
