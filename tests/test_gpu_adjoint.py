@@ -41,14 +41,16 @@ ADJ_CASES = [
 ]
 
 
-@pytest.mark.parametrize("adj_launch", [Launch(1, 4, 2, 0), Launch(1, 4, 4, 1)])
+@pytest.mark.parametrize("adj_launch", [Launch(1, 4, 2, 0), Launch(1, 4, 4, 1), Launch(2, 4, 2, 1)])
 @pytest.mark.parametrize("bits", [32, 64])
 @pytest.mark.parametrize("p,nsteps,every", ADJ_CASES)
 def test_adjoint_matches_oracle_discrete_adjoint(p, nsteps, every, bits, adj_launch):
     """dJ/deps of every cell from the GPU adjoint (FP32 states and compensated
     FP32 accumulation; per-cell arithmetic in FP32 or FP64; the register-load
-    reverse step or the bulk-copy pipelined one) within 1e-4 of the oracle's
-    FP64 adjoint, relative to max |dJ/deps|."""
+    reverse step or the bulk-copy pipelined one, 1 or 2 cells per thread)
+    within 1e-4 of the oracle's FP64 adjoint, relative to max |dJ/deps|."""
+    if p["q"] == 19 and adj_launch.cpt == 2:
+        pytest.skip("the D3Q19 reverse pipeline takes 1 cell per thread")
     shape = (p["nz"], p["ny"], p["nx"])
     eps = W.smoothed_noise(shape, 4.0, 0.4, 1.0, seed=shape[1] + nsteps)
     x_out = p["nx"] - 1
@@ -60,7 +62,7 @@ def test_adjoint_matches_oracle_discrete_adjoint(p, nsteps, every, bits, adj_lau
 
 
 @pytest.mark.parametrize("AL", [Launch(1, 4, 4, 1), Launch(2, 4, 3, 1), Launch(1, 2, 5, 1),
-                                Launch(1, 4, 2, 1)])
+                                Launch(1, 4, 2, 1), Launch(2, 4, 2, 1)])
 def test_pipelined_reverse_step_equals_register_load_kernel(AL):
     """The two reverse-step kernels run the same per-cell arithmetic and the
     same accumulation order; the compiler may contract multiply-adds
