@@ -141,3 +141,30 @@ def test_plates_on_nodes_parameters(lib):
                                                      wall_kind=1).c())) == -1
     one = (type(Params().c()) * 1)(Params(q=9, nx=8, ny=5, wall_mask=2, wall_kind=1).c())
     assert lib.vans_batch_workspace_bytes(one, 1) == 0
+
+
+def _header_struct_fields(name):
+    """Field names of `typedef struct { ... } name;` in include/vans.h, in order."""
+    import re
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    m = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + r"\s*;", src)
+    assert m, name
+    fields = []
+    for decl in m.group(1).split(";"):
+        decl = " ".join(decl.split())
+        if not decl:
+            continue
+        names = decl.split(" ", 1)[1]            # drop the type; "nx, ny, nz" or "g[3]"
+        for n in names.split(","):
+            fields.append(re.sub(r"\[.*\]", "", n).strip().lstrip("*"))
+    return fields
+
+
+def test_binding_structs_mirror_the_header():
+    """The ctypes mirrors of vans_params and vans_launch list the header's
+    fields in the header's order (a field added on one side only would shift
+    every later one)."""
+    from paper_1406_6438_gb300 import _binding as B
+    assert [f for f, _ in B._CLaunch._fields_] == _header_struct_fields("vans_launch")
+    assert [f for f, _ in B._CParams._fields_] == _header_struct_fields("vans_params")
