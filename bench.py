@@ -49,8 +49,7 @@ FALLBACK_HBM_GBS = 6800.0
 # taken on; a changed kernel or another shape reports null.
 TRAFFIC = {
     # profiles/launches_bench_4096.md: mean of two launches each
-    (4, 4, 3, 7, 2, "dd1f983c0e8dae81"): (677230336 + 561260288 + 677409280 + 559662848) // 2,
-    (4, 4, 4, 7, 0, "dd1f983c0e8dae81"): (677272832 + 561345536 + 677409792 + 559596288) // 2,
+    (4, 4, 3, 7, 2, "4071bbc4a643dc3d"): (677275392 + 561488640 + 677412096 + 559557376) // 2,
 }
 _PIPELINE_SOURCES = ("vans_step_tma.cu", "vans_pipeline.cuh", "vans_device.cuh", "vans_tma.cuh")
 KERNEL_SOURCES = {0: ("vans_step.cu", "vans_device.cuh")}
@@ -305,6 +304,10 @@ def bench_batched(torch, V, W, args=None):
            "gb_s": BYTES_PER_CELL[9] * cells * n / t / 1e9,
            "launch": vars(L), "launches": b.launch_count - c0}
     out["frac_of_peak"] = out["gb_s"] / peaks()[0]
+    if L.kind != 0:
+        # one more step with per-CTA timing records: the load balance, mean over
+        # the SMs of their busy span / the step's makespan
+        out["load_balance"] = b.profile_step()
     b.close()
     return out
 

@@ -277,6 +277,17 @@ int vans_batch_step(vans_t h, int nsteps);
 int vans_batch_moments(vans_t h, int d, float *rho_dev, float *u_dev);
 int vans_batch_get_populations(vans_t h, int d, float *f_dev);
 int vans_batch_autotune(vans_t h, vans_launch *chosen);
+
+/* One batched step (the same update as vans_batch_step(h, 1)) that also
+ * records, per CTA, {SM id, start, end} in nanoseconds of the GPU's global
+ * timer: 3 words per CTA into records_dev (device memory of `capacity` words,
+ * owned by the caller; unused slots stay 0).  With records_dev NULL only
+ * *n_records, the number of CTA slots a step can use, is set (the capacity
+ * must be 3 * *n_records).  The caller derives the load balance, e.g. the
+ * mean over SMs of their busy span over the step's makespan.  The pipelined
+ * kinds only (2, 4-7): VANS_ERR_UNSUPPORTED for kind 0. */
+int vans_batch_profile_step(vans_t h, unsigned long long *records_dev, long long capacity,
+                            long long *n_records);
 /* Cells summed over all domains. */
 long long vans_batch_cells(vans_t h);
 

@@ -159,6 +159,8 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
             "vans_batch_moments": (ctypes.c_int, [_H, ctypes.c_int, _F, _F]),
             "vans_batch_get_populations": (ctypes.c_int, [_H, ctypes.c_int, _F]),
             "vans_batch_autotune": (ctypes.c_int, [_H, _LP]),
+            "vans_batch_profile_step": (ctypes.c_int, [_H, _F, ctypes.c_longlong,
+                                                       ctypes.POINTER(ctypes.c_longlong)]),
             "vans_batch_cells": (ctypes.c_longlong, [_H]),
             "vans_cells": (ctypes.c_longlong, [_H]),
             "vans_launch_count": (ctypes.c_longlong, [_H]),
@@ -461,6 +463,29 @@ class Batch:
         c = _CLaunch()
         _check(self.lib.vans_batch_autotune(self._h, ctypes.byref(c)), "vans_batch_autotune")
         return Launch(c.cpt, c.warps, c.rows, c.kind, c.ctas)
+
+    def profile_step(self) -> dict:
+        """One step with per-CTA timing records (vans_batch_profile_step) and
+        the load balance they give: the mean over all SMs of each SM's busy span
+        (first CTA start to last CTA end on it) over the step's makespan."""
+        torch = _torch()
+        n = ctypes.c_longlong(0)
+        _check(self.lib.vans_batch_profile_step(self._h, None, 0, ctypes.byref(n)),
+               "vans_batch_profile_step")
+        rec = torch.zeros(3 * n.value, dtype=torch.int64, device=self.device)
+        _check(self.lib.vans_batch_profile_step(self._h, _ptr(rec), 3 * n.value, ctypes.byref(n)),
+               "vans_batch_profile_step")
+        r = rec.view(-1, 3).cpu().numpy()
+        r = r[r[:, 1] != 0]
+        t0, t1 = int(r[:, 1].min()), int(r[:, 2].max())
+        spans = {}
+        for sm, a, b in r:
+            lo, hi = spans.get(int(sm), (a, b))
+            spans[int(sm)] = (min(lo, a), max(hi, b))
+        sms = torch.cuda.get_device_properties(self.device).multi_processor_count
+        busy = sum(int(b) - int(a) for a, b in spans.values())
+        return {"ctas": int(len(r)), "sms_used": len(spans), "makespan_us": (t1 - t0) / 1e3,
+                "efficiency": busy / (sms * (t1 - t0))}
 
     @property
     def launch(self) -> Launch:

@@ -960,6 +960,26 @@ int vans_batch_autotune(vans_t h, vans_launch *chosen) {
     return VANS_OK;
 }
 
+int vans_batch_profile_step(vans_t h, unsigned long long *records_dev, long long capacity,
+                            long long *n_records) {
+    if (!h || !h->batched || !n_records) return VANS_ERR_ARG;
+    const long long n = (long long)h->tiles.size();    // CTAs of a step, at most
+    *n_records = n;
+    if (!records_dev) return VANS_OK;
+    if (capacity < 3 * n) return VANS_ERR_ARG;
+    for (int d = 0; d < h->n; ++d)
+        if (!h->dom_ready[d]) return VANS_ERR_STATE;
+    if (h->L.kind == 0) return VANS_ERR_UNSUPPORTED;
+    if (cudaMemsetAsync(records_dev, 0, 3 * n * sizeof(unsigned long long), h->stream) != cudaSuccess)
+        return VANS_ERR_CUDA;
+    ++h->launches;
+    if (vans::launch_ring_batched(h->doms_d, h->tiles_d, (int)n, h->parity, h->L, h->flag + 1,
+                                  h->stream, records_dev) != cudaSuccess)
+        return VANS_ERR_CUDA;
+    h->parity ^= 1;
+    return VANS_OK;
+}
+
 long long vans_batch_cells(vans_t h) {
     if (!h || !h->batched) return -1;
     long long c = 0;

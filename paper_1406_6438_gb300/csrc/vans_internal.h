@@ -67,8 +67,10 @@ cudaError_t launch_adjoint_tma(int q, const VDom &d, const float *state, const f
 // whether launch L has an instance for plates on nodes (wall_kind 1)
 bool launch_has_plates(int q, Launch L);
 // kinds 2, 4, 5: strip table (one CTA per strip); 6, 7: interleaved tile table
+// prof (nullptr: none): 3 words per CTA, {SM id, start ns, end ns}, zeroed by the caller
 cudaError_t launch_ring_batched(const VDom *doms, const Tile *strips, int nstrips, int parity,
-                                Launch L, int *status, cudaStream_t stream);
+                                Launch L, int *status, cudaStream_t stream,
+                                unsigned long long *prof = nullptr);
 cudaError_t launch_step_batched(const VDom *doms_dev, const Tile *tiles_dev, int ntiles, int parity,
                                 Launch L, int grid, cudaStream_t stream);
 int batched_blocks_per_sm(Launch L);

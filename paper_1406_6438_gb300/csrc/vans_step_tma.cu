@@ -776,11 +776,14 @@ template <int NT, int CPT, bool VEC>
 __global__ void __launch_bounds__(NT + 32) k_step_ilv_batched(const VDom *__restrict__ doms,
                                                                const Tile *__restrict__ tiles,
                                                                int ntiles, int parity, int stages,
-                                                               int *status) {
+                                                               int *status,
+                                                               unsigned long long *prof) {
     extern __shared__ __align__(128) unsigned char smem[];
+    prof_begin(prof);
     ilv_run<9, NT, CPT, VEC, false, true>(
         IlvBatchCursor(doms, tiles, (int)blockIdx.x, (int)gridDim.x, parity), status, ntiles,
         stages, smem);
+    prof_end(prof);
 }
 
 // Dynamic shared memory to request for a kernel that needs `need` bytes so
@@ -831,8 +834,10 @@ static cudaError_t launch_ilv_t(const VDom &d, const float *fin, float *fout, in
 // porosity-ring pipeline, using that domain's descriptor and buffers.
 template <int NT, int CPT, bool VEC = false, bool WS = false>
 __global__ void __launch_bounds__(WS ? NT + 32 : NT) k_step_ring_batched(
-    const VDom *__restrict__ doms, const Tile *__restrict__ strips, int parity, int stages) {
+    const VDom *__restrict__ doms, const Tile *__restrict__ strips, int parity, int stages,
+    unsigned long long *prof) {
     extern __shared__ __align__(128) unsigned char smem[];
+    prof_begin(prof);
     const Tile S = strips[blockIdx.x];   // {dom, y0, x0, y1}
     const VDom d = doms[S.dom];
     const float *fin = parity ? d.f[1] : d.f[0];
@@ -841,6 +846,7 @@ __global__ void __launch_bounds__(WS ? NT + 32 : NT) k_step_ring_batched(
         ring_strip_ws<9, NT, CPT, VEC, false, true>(d, fin, fout, S.x0, 0, S.row, S.pad, stages, smem);
     else
         ring_strip<9, NT, CPT, VEC, false, true>(d, fin, fout, S.x0, 0, S.row, S.pad, stages, smem);
+    prof_end(prof);
 }
 
 // Strips per (column block, plane): the smallest count whose grid fills the
@@ -925,7 +931,8 @@ static cudaError_t launch_tma_t(const VDom &d, const float *fin, float *fout, in
 
 template <int NT, int CPT, bool VEC = false, bool WS = false>
 static cudaError_t launch_ring_batched_t(const VDom *doms, const Tile *strips, int nstrips, int parity,
-                                         int stages, int ctas, cudaStream_t stream) {
+                                         int stages, int ctas, cudaStream_t stream,
+                                         unsigned long long *prof) {
     constexpr int TW = NT * CPT;
     const size_t smem = kBarBytes + (size_t)(stages * 9 + (stages + 2)) * (TW + 2 * kLead) * sizeof(float);
     const int max_stages = WS ? kBarBytes / 16 : kBarBytes / 8;
@@ -935,13 +942,14 @@ static cudaError_t launch_ring_batched_t(const VDom *doms, const Tile *strips, i
     auto kern = k_step_ring_batched<NT, CPT, VEC, WS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_req);
     if (e != cudaSuccess) return e;
-    kern<<<nstrips, WS ? NT + 32 : NT, smem_req, stream>>>(doms, strips, parity, stages);
+    kern<<<nstrips, WS ? NT + 32 : NT, smem_req, stream>>>(doms, strips, parity, stages, prof);
     return cudaGetLastError();
 }
 
 template <int NT, int CPT, bool VEC>
 static cudaError_t launch_ilv_batched_t(const VDom *doms, const Tile *tiles, int ntiles, int parity,
-                                        int stages, int ctas, int *status, cudaStream_t stream) {
+                                        int stages, int ctas, int *status, cudaStream_t stream,
+                                        unsigned long long *prof) {
     constexpr int TW = NT * CPT;
     const size_t smem = kBarBytes + (size_t)stages * 12 * (TW + 2 * kLead) * sizeof(float);
     if (stages < 2 || stages > kBarBytes / 16 || smem > 227 * 1024 || ntiles < 1)
@@ -958,35 +966,37 @@ static cudaError_t launch_ilv_batched_t(const VDom *doms, const Tile *tiles, int
     if (occ < 1) return cudaErrorInvalidConfiguration;
     long long grid = (long long)sms * occ;
     if (grid > ntiles) grid = ntiles;
-    kern<<<(unsigned)grid, NT + 32, smem_req, stream>>>(doms, tiles, ntiles, parity, stages, status);
+    kern<<<(unsigned)grid, NT + 32, smem_req, stream>>>(doms, tiles, ntiles, parity, stages, status,
+                                                         prof);
     return cudaGetLastError();
 }
 
 // kind 2: ring strips; 4: the same, warp-specialised; 5: warp-specialised with
 // 4 contiguous cells per thread
 cudaError_t launch_ring_batched(const VDom *doms, const Tile *strips, int nstrips, int parity,
-                                Launch L, int *status, cudaStream_t stream) {
+                                Launch L, int *status, cudaStream_t stream,
+                                unsigned long long *prof) {
     const int nt = 32 * L.warps;
     const int st = L.rows;
     if (L.kind == 6) {     // interleaved tile table, strided cells
         if (nt == 128 && L.cpt == 2)
-            return launch_ilv_batched_t<128, 2, false>(doms, strips, nstrips, parity, st, L.ctas, status, stream);
+            return launch_ilv_batched_t<128, 2, false>(doms, strips, nstrips, parity, st, L.ctas, status, stream, prof);
         if (nt == 256 && L.cpt == 2)
-            return launch_ilv_batched_t<256, 2, false>(doms, strips, nstrips, parity, st, L.ctas, status, stream);
+            return launch_ilv_batched_t<256, 2, false>(doms, strips, nstrips, parity, st, L.ctas, status, stream, prof);
         return cudaErrorInvalidValue;
     }
     if (L.kind == 7) {     // interleaved tile table, 4 consecutive cells
         if (nt == 64 && L.cpt == 4)
-            return launch_ilv_batched_t<64, 4, true>(doms, strips, nstrips, parity, st, L.ctas, status, stream);
+            return launch_ilv_batched_t<64, 4, true>(doms, strips, nstrips, parity, st, L.ctas, status, stream, prof);
         if (nt == 128 && L.cpt == 4)
-            return launch_ilv_batched_t<128, 4, true>(doms, strips, nstrips, parity, st, L.ctas, status, stream);
+            return launch_ilv_batched_t<128, 4, true>(doms, strips, nstrips, parity, st, L.ctas, status, stream, prof);
         return cudaErrorInvalidValue;
     }
     if (L.kind == 5) {
         if (nt == 64 && L.cpt == 4)
-            return launch_ring_batched_t<64, 4, true, true>(doms, strips, nstrips, parity, st, L.ctas, stream);
+            return launch_ring_batched_t<64, 4, true, true>(doms, strips, nstrips, parity, st, L.ctas, stream, prof);
         if (nt == 128 && L.cpt == 4)
-            return launch_ring_batched_t<128, 4, true, true>(doms, strips, nstrips, parity, st, L.ctas, stream);
+            return launch_ring_batched_t<128, 4, true, true>(doms, strips, nstrips, parity, st, L.ctas, stream, prof);
         return cudaErrorInvalidValue;
     }
     if (L.kind != 2 && L.kind != 4) return cudaErrorInvalidValue;
@@ -994,8 +1004,8 @@ cudaError_t launch_ring_batched(const VDom *doms, const Tile *strips, int nstrip
 #define VANS_RB_CASE(NTT, CC)                                                                   \
     if (nt == NTT && L.cpt == CC)                                                               \
         return ws ? launch_ring_batched_t<NTT, CC, false, true>(doms, strips, nstrips, parity, st, L.ctas, \
-                                                               stream)                        \
-                  : launch_ring_batched_t<NTT, CC>(doms, strips, nstrips, parity, st, L.ctas, stream);
+                                                               stream, prof)                        \
+                  : launch_ring_batched_t<NTT, CC>(doms, strips, nstrips, parity, st, L.ctas, stream, prof);
     VANS_RB_CASE(128, 2)
     VANS_RB_CASE(128, 4)
     VANS_RB_CASE(256, 1)

@@ -97,4 +97,26 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return false;
 }
 
+// Per-CTA timing records of a profiled batched step: {SM id, start ns, end ns}
+// per CTA (%globaltimer, one clock for the whole GPU).  Thread 0 writes the
+// first two; the lane 0 of every warp raises the third as its warp finishes.
+__device__ __forceinline__ void prof_begin(unsigned long long *prof) {
+    if (prof && threadIdx.x == 0) {
+        unsigned int sm;
+        unsigned long long t;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        prof[3 * blockIdx.x] = sm;
+        prof[3 * blockIdx.x + 1] = t;
+    }
+}
+
+__device__ __forceinline__ void prof_end(unsigned long long *prof) {
+    if (prof && (threadIdx.x & 31) == 0) {
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        atomicMax(&prof[3 * blockIdx.x + 2], t);
+    }
+}
+
 }  // namespace vans

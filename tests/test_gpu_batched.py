@@ -94,3 +94,28 @@ def test_batched_domains_with_moving_walls(L):
         _, u_o, f_o = oracle_run(p, eps, 60)
         f = b.populations(d).cpu().numpy()
         assert np.abs(f - f_o).max() <= 5e-7, (L, d)
+
+
+@pytest.mark.parametrize("L", [Launch(2, 4, 3, 2), Launch(2, 4, 3, 4), Launch(4, 4, 2, 7),
+                               Launch(4, 4, 2, 5, 2)])
+def test_profiled_step_equals_a_step(L):
+    """vans_batch_profile_step advances the batch exactly like one step (every
+    population bitwise) and returns one timing record per CTA, from which the
+    load balance lies in (0, 1]; the register-load kind has no records."""
+    torch = torch_cuda()
+    from paper_1406_6438_gb300._binding import VansError
+    doms = W.batched_channels(n=9, seed=43, nx_range=(40, 700), ny_range=(8, 90))
+    a, b = _batch(doms), _batch(doms)
+    a.launch = L
+    b.launch = L
+    a.step(3)
+    b.step(2)
+    lb = b.profile_step()
+    torch.cuda.synchronize()
+    for d in range(len(doms)):
+        assert torch.equal(a.populations(d), b.populations(d)), d
+    assert lb["ctas"] > 0 and lb["sms_used"] > 0
+    assert 0.0 < lb["efficiency"] <= 1.0 and lb["makespan_us"] > 0.0
+    b.launch = Launch(4, 4, 1)
+    with pytest.raises(VansError):
+        b.profile_step()
