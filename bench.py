@@ -503,6 +503,13 @@ def main():
         cpu = {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
                "sample": f"FP64 oracle, {n_or} steps of the full {args.n}x{args.n} workload "
                          f"({dt:.1f} s)", "cpu": cpu_model()}
+        O.set_num_threads(1)                   # the same oracle on one core
+        try:
+            m1, n1, dt1, _ = oracle_mlups(p, eps, budget_s=4.0, max_steps=2)
+        finally:
+            O.set_num_threads(cores)
+        cpu["single_thread"] = {"value": m1, "unit": "MLUPS", "cores": 1,
+                                "sample": f"{n1} step(s) of the same workload ({dt1:.1f} s)"}
 
     clocks = clk.summary()
     line = {
