@@ -484,8 +484,12 @@ class Batch:
             spans[int(sm)] = (min(lo, a), max(hi, b))
         sms = torch.cuda.get_device_properties(self.device).multi_processor_count
         busy = sum(int(b) - int(a) for a, b in spans.values())
+        per_sm = {}
+        for sm in r[:, 0]:
+            per_sm[int(sm)] = per_sm.get(int(sm), 0) + 1
         return {"ctas": int(len(r)), "sms_used": len(spans), "makespan_us": (t1 - t0) / 1e3,
-                "efficiency": busy / (sms * (t1 - t0))}
+                "efficiency": busy / (sms * (t1 - t0)),
+                "max_ctas_per_sm": max(per_sm.values())}
 
     @property
     def launch(self) -> Launch:

@@ -119,3 +119,16 @@ def test_profiled_step_equals_a_step(L):
     b.launch = Launch(4, 4, 1)
     with pytest.raises(VansError):
         b.profile_step()
+
+
+def test_cta_cap_holds():
+    """A persistent batched launch capped at 2 CTAs per SM puts at most 2 on any
+    SM (from the profiled step's records); uncapped, the same shape fits more."""
+    torch_cuda()
+    doms = W.batched_channels(n=24, seed=44, nx_range=(200, 900), ny_range=(40, 200))
+    b = _batch(doms)
+    b.launch = Launch(4, 4, 2, 7, 2)
+    capped = b.profile_step()
+    b.launch = Launch(4, 4, 2, 7)
+    free = b.profile_step()
+    assert capped["max_ctas_per_sm"] <= 2 < free["max_ctas_per_sm"]
