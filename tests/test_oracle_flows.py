@@ -163,6 +163,42 @@ def test_forchheimer_channel_against_bvp():
     assert 0.95 < Re < 1.05
 
 
+@pytest.mark.parametrize("k_mode", [2, 0])
+def test_d3q19_forchheimer_channel_against_bvp(k_mode):
+    """D3Q19 with walls in y only (periodic x and z) reduces to the same 1-D
+    porous channel equation as D2Q9: uniform eps = 0.6, Darcy and Forchheimer
+    drag (K = Da H^2 with F_eps from eps, or the Ergun K(eps) and F_eps(eps)),
+    Re = U H / nu = 1.  Its steady profile meets the Newton solution of
+    nu u'' - (eps nu/K) u - (eps^2 F_eps/sqrt K) |u| u + g = 0 within 1 % at
+    H = 64, with the error shrinking at least 2.5x from H = 32 (the D3Q19
+    weights, P_i and F_i and the drag solve all enter)."""
+    tau, e = 0.8, 0.6
+    nu = CS2 * (tau - 0.5)
+    Feps = 1.75 / np.sqrt(150 * e ** 3)
+    errs = []
+    for H in (32, 64):
+        if k_mode == 2:
+            K, extra = 1e-3 * H * H, dict(K=1e-3 * H * H)
+        else:
+            d_p = np.sqrt(1e-3 * H * H * 150 * (1 - e) ** 2 / e ** 3)   # Ergun K(eps) = Da H^2
+            K, extra = e ** 3 * d_p ** 2 / (150 * (1 - e) ** 2), dict(d_p=float(d_p))
+        U = nu / H
+        g = U * e * nu / K + e ** 2 * Feps / np.sqrt(K) * U * U
+        p = O.Params(q=19, nx=1, ny=H, nz=2, wall_mask=2, tau=tau, g=(g, 0, 0), drag_mode=2,
+                     k_mode=k_mode, **extra)
+        eps = np.full(p.shape, e)
+        f = O.run(p, eps, O.init(p, eps), 6000)
+        _, u = O.moments(p, eps, f)
+        assert np.abs(u[0] - u[0, :1]).max() <= 1e-12 * np.abs(u[0]).max()   # uniform in z
+        assert np.abs(u[1:]).max() <= 1e-12 * np.abs(u[0]).max()
+        yb, ub = porous_bvp(nu, e, K, Feps, g, H)
+        y = np.arange(H) + 0.5
+        ref = np.interp(y, yb, ub)
+        errs.append(np.abs(u[0, 0, :, 0] - ref).max() / ref.max())
+    assert errs[1] < 1e-2, errs
+    assert errs[0] / errs[1] > 2.5, errs
+
+
 def test_uniform_eps_scaling_invariance():
     """With eps uniform the scheme is linear-homogeneous in f: the run with eps,
     drag (alpha, beta) and force per mass g equals eps times the eps = 1 run with
