@@ -61,6 +61,24 @@ def test_duct_256cubed_every_cell_after_4_steps():
     assert np.abs(rho.cpu().numpy() - rho_o).max() <= 1e-6
 
 
+def test_duct_256cubed_long_run_properties():
+    """The duct's 500 steps (the workload's length) in the autotuned launch:
+    finite, subsonic, mass conserved to FP32 rounding (bounce-back walls and a
+    body force conserve it), and the monitoring step's reductions agree."""
+    torch = torch_cuda()
+    p, eps, n = W.duct_3d()
+    s = _autotuned(p, eps)
+    m0 = s.populations().double().sum().item()
+    rho, u, st = s.step_monitored(n, n)
+    m1 = s.populations().double().sum().item()
+    assert s.check()
+    stats = st.cpu().numpy()
+    assert stats[2] == 0.0 and stats[3] == 1.0 and 0.0 < stats[1] < 0.3
+    assert abs(m1 - m0) <= 1e-6 * m0
+    speed = float(u.double().pow(2).sum(0).sqrt().max().item())
+    assert abs(speed - float(stats[1])) <= 1e-5 * float(stats[1])
+
+
 def test_batched_256_domains_sampled():
     """The 256-domain batch in its autotuned configuration: eight domains
     (the largest, the smallest and six drawn with a seed) against the oracle
