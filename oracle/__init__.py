@@ -30,6 +30,10 @@ _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libvans_oracle.so")
 _lock = threading.Lock()
 _lib = None
+# The test of the pins (tests/test_oracle_mutants.py) points this module at a
+# build of the oracle with one mistake planted in it, in a child process of its
+# own; nothing else sets this variable.
+_MUTANT = os.environ.get("VANS_ORACLE_MUTANT_LIB")
 
 
 def build(force: bool = False) -> str:
@@ -102,8 +106,7 @@ def _load():
     with _lock:
         if _lib is not None:
             return _lib
-        build()
-        lib = ctypes.CDLL(_LIB_PATH)
+        lib = ctypes.CDLL(_MUTANT if _MUTANT else build())
         P = ctypes.POINTER(_Params)
         d = ctypes.POINTER(ctypes.c_double)
         i = ctypes.POINTER(ctypes.c_int)
