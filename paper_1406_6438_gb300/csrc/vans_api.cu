@@ -334,18 +334,36 @@ int set_batch_launch(vans_t h, const Launch &L) {
     return VANS_OK;
 }
 
-// Fastest of three timed trials of `reps` launches each (after two untimed),
-// so one noisy trial does not decide the pick.
+// Fastest of three timed trials (after two untimed) of `reps` launches
+// replayed as one CUDA graph, as run_steps issues them: one noisy trial does
+// not decide the pick, and small domains are not judged by a launch overhead
+// that the graph replay does not pay.  fn(stream) issues one launch; a shape
+// that fails to launch or capture scores 1e30.
 template <class F>
 float time_launches(vans_t h, F &&fn, int reps) {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    if (cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return 1e30f;
+    }
+    bool ok = true;
+    for (int i = 0; i < reps && ok; ++i) ok = fn(h->cap) == cudaSuccess;
+    const cudaError_t ec = cudaStreamEndCapture(h->cap, &g);
+    if (!ok || ec != cudaSuccess || cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return 1e30f;
+    }
+    cudaGraphDestroy(g);
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
-    for (int i = 0; i < 2; ++i) fn();
+    for (int i = 0; i < 2; ++i) cudaGraphLaunch(ge, h->stream);
     float best = 1e30f;
     for (int trial = 0; trial < 3; ++trial) {
         cudaEventRecord(a, h->stream);
-        for (int i = 0; i < reps; ++i) fn();
+        cudaGraphLaunch(ge, h->stream);
         cudaEventRecord(b, h->stream);
         cudaEventSynchronize(b);
         float ms = 0.f;
@@ -355,6 +373,7 @@ float time_launches(vans_t h, F &&fn, int reps) {
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
+    cudaGraphExecDestroy(ge);
     return best;
 }
 
@@ -621,8 +640,9 @@ int vans_autotune(vans_t h, vans_launch *chosen) {
     for (const Launch &L : cs) {
         if (h->dom.nee && !vans::launch_has_plates(h->q, L)) continue;   // no plate instance
         const float ms = time_launches(
-            h, [&] { vans::launch_step(h->q, h->dom, in, outb, L, h->stream); }, reps);
-        h->launches += 3 * reps + 2;
+            h, [&](cudaStream_t st) { return vans::launch_step(h->q, h->dom, in, outb, L, st); },
+            reps);
+        h->launches += 5 * reps;
         if (ms < best_ms) {
             best_ms = ms;
             best = L;
@@ -940,8 +960,9 @@ int vans_batch_autotune(vans_t h, vans_launch *chosen) {
     for (const Launch &L : candidates(9, true)) {
         if (set_batch_launch(h, L) != VANS_OK) continue;
         // reads the current parity and writes the other buffer of every domain
-        const float ms = time_launches(h, [&] { batched_step(h, h->stream, par); }, 5);
-        h->launches += 17;
+        const float ms =
+            time_launches(h, [&](cudaStream_t st) { return batched_step(h, st, par); }, 5);
+        h->launches += 25;
         if (ms < best_ms) {
             best_ms = ms;
             best = L;
