@@ -201,7 +201,8 @@ int vans_get_state(vans_t h, float *state_dev);
 int vans_set_state(vans_t h, const float *state_dev);
 
 /* Pick the fastest launch configuration for this domain by timing candidates
- * on the handle's own buffers (the state is not changed).  Synchronises.
+ * on the handle's own buffers (the state is not changed), each as a CUDA graph
+ * of its launches replayed the way vans_step issues them.  Synchronises.
  * `chosen` may be NULL. */
 int vans_autotune(vans_t h, vans_launch *chosen);
 
@@ -276,6 +277,8 @@ int vans_batch_set_eps(vans_t h, int d, const float *eps_dev);
 int vans_batch_step(vans_t h, int nsteps);
 int vans_batch_moments(vans_t h, int d, float *rho_dev, float *u_dev);
 int vans_batch_get_populations(vans_t h, int d, float *f_dev);
+/* vans_autotune for the batch: the candidates are timed the same way, and the
+ * step tables rebuilt for the pick. */
 int vans_batch_autotune(vans_t h, vans_launch *chosen);
 
 /* One batched step (the same update as vans_batch_step(h, 1)) that also
