@@ -168,3 +168,22 @@ def test_binding_structs_mirror_the_header():
     from paper_1406_6438_gb300 import _binding as B
     assert [f for f, _ in B._CLaunch._fields_] == _header_struct_fields("vans_launch")
     assert [f for f, _ in B._CParams._fields_] == _header_struct_fields("vans_params")
+
+
+@pytest.mark.parametrize("lang,std", [("c", "-std=c99"), ("c++", "-std=c++17")])
+def test_header_compiles_as_plain_c_and_cpp(tmp_path, lang, std):
+    """include/vans.h is a plain C header (C99 types only) usable from C++
+    too: a translation unit that declares every struct compiles warning-free."""
+    import shutil
+    import subprocess
+    cc = "gcc" if lang == "c" else "g++"
+    if shutil.which(cc) is None:
+        pytest.skip(cc + " not found")
+    src = tmp_path / "use_vans.c"
+    src.write_text('#include "vans.h"\n'
+                   "int main(void) { vans_params p; vans_launch l; (void)p; (void)l;\n"
+                   "  return (int)sizeof(vans_launch); }\n")
+    r = subprocess.run([cc, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-x", lang,
+                        "-I", os.path.join(ROOT, "include"), "-c", str(src), "-o",
+                        str(tmp_path / "use_vans.o")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
