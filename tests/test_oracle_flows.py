@@ -338,6 +338,28 @@ def test_porous_couette_with_nee_plates_against_bvp(Re, Da, steps):
     assert np.abs(u[0, 0, :, 0] - ref).max() <= 4e-3 * u0
 
 
+@pytest.mark.parametrize("q", [9, 19])
+def test_plate_nodes_at_rest_hold_the_plate_equilibrium(q):
+    """Reading R9 of the oracle (the paper's non-equilibrium extrapolation) at
+    rho = 1: with eps(y) chosen so that grad eps vanishes on the fluid rows next
+    to the plates (eps of the plate row equals eps two rows in), those rows are
+    at rest, f = w_i eps, and a plate node holds exactly f^eq(eps_b, 1, u_b) =
+    w_i eps_b [1 + 3 e_i.u_b + 4.5 (e_i.u_b)^2 - 1.5 u_b.u_b] (Eq. d2q9eq) with
+    its own porosity eps_b, not its neighbour's."""
+    nz = 1 if q == 9 else 3
+    uw = (0.02, 0.0, 0.0) if q == 9 else (0.02, 0.0, -0.01)
+    prof = np.array([0.45, 0.8, 0.45, 0.6, 0.9, 0.6])       # eps(y), rows 0..5
+    p = O.Params(q=q, nx=7, ny=6, nz=nz, wall_mask=2, wall_kind=1, tau=0.8, u_wall=uw)
+    eps = np.broadcast_to(prof[None, :, None], p.shape).copy()
+    f = O.init(p, eps)
+    e, w, _ = O.lattice(q)
+    eu = e @ np.asarray(uw)
+    want = w[:, None, None, None] * eps[None]
+    want[:, :, -1, :] = (w * (1 + 3 * eu + 4.5 * eu ** 2 - 1.5 * np.dot(uw, uw)))[:, None, None] \
+        * prof[-1]
+    assert np.abs(f - want).max() <= 1e-15
+
+
 def test_nee_parameters_validated():
     eps = np.ones((1, 5, 4))
     for bad in (dict(wall_mask=0), dict(wall_mask=3), dict(ny=2), dict(wall_kind=2)):

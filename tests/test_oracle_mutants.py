@@ -72,7 +72,23 @@ MUTANTS = [
      "ubar[k] += c->alpha * Fbar[k] - c->beta * c->un * Fbar[k];"),
     ("adjoint: eps partial of rho = R / eps dropped",
      "*epsbar += -rhobar * c->R / (eps * eps);", "*epsbar += 0.0 * rhobar;"),
+    ("adjoint: transposed grad-eps stencil with the wrong sign", "epsbar[t] += s / CS2;",
+     "epsbar[t] -= s / CS2;"),
+    ("drag: fixed-K Forchheimer power of eps", "b = eps * eps * eps * p->F_eps / sqrt(p->K);",
+     "b = eps * eps * p->F_eps / sqrt(p->K);"),
+    ("velocity: |m| for every component", "for (int k = 0; k < 3; ++k) u[k] = 2.0 * m[k] / D;",
+     "for (int k = 0; k < 3; ++k) u[k] = 2.0 * mm / D;"),
+    ("streaming: periodic wrap off by one", "t = (t + n) % n;", "t = (t + n - 1) % n;"),
+    ("plates on nodes: plate equilibrium with the fluid node's eps",
+     "equilibrium(L, eps[nb_], c.rho, ub, feqb);", "equilibrium(L, eps[nf], c.rho, ub, feqb);"),
+    ("plates on nodes: upper plate at rest",
+     "equilibrium(L, eps[n], R / eps[n], y == 0 ? zero : p->u_wall, feq);",
+     "equilibrium(L, eps[n], R / eps[n], zero, feq);"),
 ]
+# Not among them: the rule for a D3Q19 population that crosses the moving y
+# wall and a z wall at once (reading R7 of the oracle: plain bounce-back).  The
+# other choice converges to the same continuum flow, so no closed form can
+# decide it; the GPU follows the oracle's choice and the parity tests hold it.
 
 
 def _compile(src: str, out: str) -> None:
