@@ -199,6 +199,66 @@ def test_d3q19_forchheimer_channel_against_bvp(k_mode):
     assert errs[0] / errs[1] > 2.5, errs
 
 
+def _equivariance_err(u_a, u_b):
+    return np.abs(u_a - u_b).max() / np.abs(u_a).max()
+
+
+def test_transpose_equivariance_d2q9_nonuniform_eps():
+    """The D2Q9 lattice is symmetric under x <-> y, so on a periodic square
+    with any eps field, swapping the axes of eps and of the body force swaps
+    the axes of the flow after any number of steps (to rounding: the sums over
+    directions run in another order).  Non-uniform eps, Darcy + Forchheimer."""
+    n = 12
+    eps = W.smoothed_noise((1, n, n), 2.0, 0.4, 1.0, seed=21).astype(np.float64)
+    kw = dict(q=9, nx=n, ny=n, wall_mask=0, tau=0.7, drag_mode=2, k_mode=0, d_p=6.0)
+    pa = O.Params(g=(4e-5, 1.5e-5, 0), **kw)
+    pb = O.Params(g=(1.5e-5, 4e-5, 0), **kw)
+    eb = np.ascontiguousarray(eps.transpose(0, 2, 1))
+    _, ua = O.moments(pa, eps, O.run(pa, eps, O.init(pa, eps), 40))
+    _, ub = O.moments(pb, eb, O.run(pb, eb, O.init(pb, eb), 40))
+    swapped = np.stack([ub[1].transpose(0, 2, 1), ub[0].transpose(0, 2, 1)])
+    assert _equivariance_err(ua, swapped) <= 1e-12
+
+
+def test_mirror_equivariance_channel_nonuniform_eps():
+    """Bounce-back walls on both y faces are mirror images of each other, so
+    mirroring eps in y mirrors the flow: u_x(y) -> u_x(ny-1-y), u_y -> -u_y
+    (D2Q9 and D3Q19, non-uniform eps, drag on, body force along x)."""
+    for q, shape, wm in ((9, (1, 10, 9), 2), (19, (5, 8, 6), 6)):
+        nz, ny, nx = shape
+        eps = W.smoothed_noise(shape, 1.5, 0.4, 1.0, seed=22).astype(np.float64)
+        p = O.Params(q=q, nx=nx, ny=ny, nz=nz, wall_mask=wm, tau=0.7, g=(4e-5, 0, 0),
+                     drag_mode=2, k_mode=0, d_p=6.0)
+        em = np.ascontiguousarray(eps[:, ::-1, :])
+        _, ua = O.moments(p, eps, O.run(p, eps, O.init(p, eps), 40))
+        _, ub = O.moments(p, em, O.run(p, em, O.init(p, em), 40))
+        mir = ub[:, :, ::-1, :].copy()
+        mir[1] *= -1
+        assert _equivariance_err(ua, mir) <= 1e-12, q
+
+
+def test_axis_cycle_equivariance_d3q19_nonuniform_eps():
+    """D3Q19 is symmetric under the cyclic exchange of axes: on a periodic cube,
+    mapping every point (x, y, z) to (y, z, x), with eps carried along and the
+    force turned to (g_y, g_z, g_x), maps the flow the same way."""
+    n = 6
+    eps = W.smoothed_noise((n, n, n), 1.5, 0.4, 1.0, seed=23).astype(np.float64)
+    kw = dict(q=19, nx=n, ny=n, nz=n, wall_mask=0, tau=0.7, drag_mode=2, k_mode=0, d_p=6.0)
+    g = (3e-5, 1e-5, -2e-5)
+    pa = O.Params(g=g, **kw)
+    pb = O.Params(g=(g[1], g[2], g[0]), **kw)
+    # arrays are [z, y, x]: the image field B[z', y', x'] = A[z, y, x] with
+    # x' = y, y' = z, z' = x, i.e. B[i, j, k] = A[j, k, i]
+    eb = np.ascontiguousarray(np.transpose(eps, (2, 0, 1)))
+    assert eb[1, 2, 3] == eps[2, 3, 1]
+    _, ua = O.moments(pa, eps, O.run(pa, eps, O.init(pa, eps), 30))
+    _, ub = O.moments(pb, eb, O.run(pb, eb, O.init(pb, eb), 30))
+    back = lambda a: np.transpose(a, (1, 2, 0))       # B -> A
+    # the image's x', y', z' components are the original's y, z, x components
+    orig = np.stack([back(ub[2]), back(ub[0]), back(ub[1])])
+    assert _equivariance_err(ua, orig) <= 1e-12
+
+
 def test_uniform_eps_scaling_invariance():
     """With eps uniform the scheme is linear-homogeneous in f: the run with eps,
     drag (alpha, beta) and force per mass g equals eps times the eps = 1 run with
