@@ -247,7 +247,8 @@ int vans_adjoint_segment(vans_t h, const float *ckpt, float *seg, int len, float
 
 /* Launch shape of the reverse step.  kind 0: register-load kernel, cpt cells
  * per lane (1, or 2 for D2Q9), `warps` x `rows` threads per block (at most 8
- * warps).  kind 1 (the default, cpt 1, 4 warps, 4 stages): bulk-copy pipeline
+ * warps).  kind 1 (the default: cpt 1, 4 warps, 4 stages for D2Q9, 2 for
+ * D3Q19): bulk-copy pipeline
  * with a producer warp, persistent CTAs over the row tiles; `warps` compute
  * warps (D2Q9: 2 with cpt 1, or 4 with cpt 1 or 2; D3Q19: 4 with cpt 1),
  * `rows` = pipeline stages (2..8); ctas must be 0.  VANS_ERR_ARG otherwise. */

@@ -464,7 +464,7 @@ int vans_create(const vans_params *p, void *workspace, size_t workspace_bytes, v
     h->L = (p->q == 9) ? Launch{4, 4, 1, 0} : Launch{2, 4, 1, 0};
     // the pipelined reverse step, one cell per thread, 4 stages: fastest on GB300 at 512^2
     // (backward pass 17.4 us per step against 20.8 with the register-load kernel)
-    h->adjL = Launch{1, 4, 4, 1};
+    h->adjL = (p->q == 19) ? Launch{1, 4, 2, 1} : Launch{1, 4, 4, 1};   // D3Q19: 0.78 vs 0.61 of HBM
     int rc = make_streams(h, cuda_stream);
     if (rc) {
         vans_destroy(h);

@@ -41,7 +41,8 @@ ADJ_CASES = [
 ]
 
 
-@pytest.mark.parametrize("adj_launch", [Launch(1, 4, 2, 0), Launch(1, 4, 4, 1), Launch(2, 4, 2, 1)])
+@pytest.mark.parametrize("adj_launch", [Launch(1, 4, 2, 0), Launch(1, 4, 4, 1), Launch(1, 4, 2, 1),
+                                        Launch(2, 4, 2, 1)])
 @pytest.mark.parametrize("bits", [32, 64])
 @pytest.mark.parametrize("p,nsteps,every", ADJ_CASES)
 def test_adjoint_matches_oracle_discrete_adjoint(p, nsteps, every, bits, adj_launch):
