@@ -9,6 +9,8 @@ import torch.multiprocessing as mp
 
 import bench
 
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
 
 def _free_port():
     s = socket.socket()
@@ -57,3 +59,20 @@ def test_reference_arm_idles_on_nonzero_ranks(monkeypatch):
         steps, warmup, gpus = 5, 3, 2
 
     assert bench.reference_arm(A()) == 0
+
+
+def test_reference_arm_prints_one_json_line_on_cpu():
+    """`bench.py --impl reference` (the FP64 oracle on host cores) needs no GPU
+    and prints one JSON line with the keys the contract names."""
+    import json
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "MLUPS" and d["value"] > 0
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+    assert d["higher_is_better"] is True and d["steps"] == 1
