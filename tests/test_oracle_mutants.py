@@ -15,7 +15,8 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "vans_oracle.c")
-PINS = ["tests/test_oracle_cell.py", "tests/test_oracle_flows.py", "tests/test_oracle_adjoint.py"]
+PINS = ["tests/test_oracle_cell.py", "tests/test_oracle_flows.py", "tests/test_oracle_adjoint.py",
+        "tests/test_oracle_flux.py"]
 
 # name, text in the oracle, planted mistake (each text occurs exactly once)
 MUTANTS = [
@@ -84,6 +85,15 @@ MUTANTS = [
     ("plates on nodes: upper plate at rest",
      "equilibrium(L, eps[n], R / eps[n], y == 0 ? zero : p->u_wall, feq);",
      "equilibrium(L, eps[n], R / eps[n], zero, feq);"),
+    ("flux: the populations' momentum without the half-force terms of Eq. 1moment",
+     "s += c.R * c.u[0];", "s += c.j[0];"),
+    ("flux: rho u_x instead of eps rho u_x", "s += c.R * c.u[0];", "s += c.rho * c.u[0];"),
+    ("flux: the plane next to the outlet",
+     "p->nx + x_out;\n            double fc[19], gc[3] = {grad[n], grad[N + n], grad[2 * N + n]};\n"
+     "            cell_t c;",
+     "p->nx + (x_out + 1) % p->nx;\n            double fc[19], gc[3] = {grad[n], grad[N + n], "
+     "grad[2 * N + n]};\n            cell_t c;"),
+    ("flux: the y component", "s += c.R * c.u[0];", "s += c.R * c.u[1];"),
 ]
 # Not among them: the rule for a D3Q19 population that crosses the moving y
 # wall and a z wall at once (reading R7 of the oracle: plain bounce-back).  The
