@@ -92,22 +92,23 @@ typedef struct {
 /* Launch configuration of the step kernels (chosen by vans_autotune).
  * kind 0: register-load kernel: cpt cells per lane (1, 2, 4), `warps` warps
  *         along x times `rows` rows per block (warps*rows <= 8).
- * kind 1: bulk-copy pipeline kernel (persistent CTAs, rows staged in shared
- *         memory by cp.async.bulk): 32*warps threads (warps 4 or 8), cpt cells
- *         per thread per tile (1, 2, 4), `rows` = pipeline stages (2..6).
- * kind 2: the kind-1 pipeline where each CTA walks a strip of consecutive rows
- *         (one column block, one z plane) and keeps the porosity rows in a
- *         shared-memory ring, so each eps row is read from HBM once per strip.
- * kind 3: kind 2 with each thread on consecutive cells (D2Q9: cpt 4, D3Q19:
- *         cpt 2; warps 2 or 4): 16- or 8-byte shared loads and global stores.
- * kind 4, 5: kinds 2 and 3 with one extra producer warp per CTA (warps counts
- *         the compute warps only): stages are released per warp through
- *         "empty" mbarriers instead of a block-wide barrier per tile.
+ * kind 2: bulk-copy pipeline (rows staged in shared memory by cp.async.bulk),
+ *         32*warps threads (warps 4 or 8), cpt cells per thread per tile
+ *         (1, 2, 4), `rows` = pipeline stages (2..6); each CTA walks a strip
+ *         of consecutive rows (one column block, one z plane) and keeps the
+ *         porosity rows in a shared-memory ring, so each eps row is read from
+ *         HBM once per strip.
+ * kind 4, 5: kind 2 with one extra producer warp per CTA (warps counts the
+ *         compute warps only): stages are released per warp through "empty"
+ *         mbarriers instead of a block-wide barrier per tile; kind 5 puts each
+ *         thread on consecutive cells (D2Q9: cpt 4, D3Q19: cpt 2; warps 2 or 4)
+ *         with 16- or 8-byte shared loads and global stores.
  * kind 6, 7: persistent CTAs that take tiles b, b+G, b+2G, ... of the row-major
  *         tile order (the whole grid sweeps one band of rows), porosity rows
  *         staged per tile, producer warp as in kinds 4, 5; 6 strided cells
  *         (D2Q9 cpt 2, D3Q19 cpt 1; warps 4 or 8), 7 consecutive cells as in
- *         kind 3.
+ *         kind 5.
+ * Kinds 1 and 3 are not built (VANS_ERR_ARG).
  *         The batched path takes kinds 0, 2, 4 and 5 (one CTA per strip of
  *         up to 32 rows of one domain) and 6, 7 (one table of every domain's
  *         row tiles); the batch is D2Q9 only. */
@@ -116,7 +117,7 @@ typedef struct {
     int warps;
     int rows;
     int kind;
-    int ctas;   /* kinds 1-7: at most this many CTAs per SM (1..4; the
+    int ctas;   /* kinds 2-7: at most this many CTAs per SM (1..4; the
                    dynamic shared memory request is raised until no more
                    fit), 0 = as many as fit; kind 0: must be 0 */
 } vans_launch;
@@ -151,6 +152,15 @@ void vans_destroy(vans_t h);
  * satisfy 0 < eps <= 1; otherwise VANS_ERR_ARG and the handle keeps its
  * previous state.  (Synchronises the stream once to check the range.) */
 int vans_set_eps(vans_t h, const float *eps_dev);
+
+/* vans_set_eps without the stream synchronisation, for pipelines that run
+ * one job per porosity field back to back: the range check runs on the device
+ * in the same pass that pads eps, and does not stop the reset.  If a value is
+ * outside (0, 1] the state is undefined and the next vans_check (which
+ * synchronises) returns VANS_ERR_ARG; the next vans_set_eps or
+ * vans_set_eps_async with a valid field clears that.  Otherwise identical to
+ * vans_set_eps. */
+int vans_set_eps_async(vans_t h, const float *eps_dev);
 
 /* Replace the porosity field by eps_dev (dense, 0 < eps <= 1 else
  * VANS_ERR_ARG and nothing changes) while keeping the physical populations
@@ -297,9 +307,9 @@ long long vans_batch_cells(vans_t h);
 
 /* ------------------------------------------------- no-allocation step --- */
 
-/* One step from state_in to state_out (vans_state_floats(p) floats each,
- * distinct buffers; without a moving wall an all-zero buffer is the rest
- * state f = w eps) for a
+/* One step from state_in to state_out (vans_state_floats(p) floats each;
+ * the two ranges must not overlap, else VANS_ERR_ARG; without a moving wall
+ * an all-zero buffer is the rest state f = w eps) for a
  * caller that cannot allocate device memory or hand the library a workspace:
  * code that runs inside another framework's memory pool or allocator, code that
  * may not call cudaMalloc while a CUDA graph is being captured, or an embedded
@@ -309,8 +319,9 @@ long long vans_batch_cells(vans_t h);
  * range-checked here), is a 16 MiB array that the library holds in device
  * memory on every GPU where it is loaded, until the process exits.
  * Limit: ny*nz rows times the padded row length (nx rounded up to 128, plus 9,
- * rounded up to 32 floats) must not exceed 4 Mi floats, e.g. up to about a
- * 2000 x 2000 D2Q9 or a 150^3 D3Q19 domain; larger domains get VANS_ERR_ARG.
+ * rounded up to 32 floats) must not exceed 4 Mi floats, e.g. a D2Q9 domain of
+ * 2048 x 2016 cells, or a D3Q19 cube of up to 128^3 (from 129 cells on the
+ * padded row jumps to 288 floats); larger domains get VANS_ERR_ARG.
  * Parameter errors as in vans_create.  The first call on a device looks up the
  * array's device address; make that first call before any stream capture.
  * All calls share the array, so calls whose GPU work overlaps (on different
@@ -318,6 +329,47 @@ long long vans_batch_cells(vans_t h);
  * no counterpart to this entry point. */
 int vans_step_static(const vans_params *p, const float *eps_dev, const float *state_in,
                      float *state_out, void *cuda_stream);
+
+/* -------------------------------------------------- slabs along x --- */
+/* A domain too large for one GPU is cut along x, its periodic axis, into
+ * slabs of whole columns, one handle per slab (each created with its own nx).
+ * The paper credits the scheme's explicit update with its parallelism
+ * (abstract and introduction): in the final LBE a cell's next populations
+ * come from its neighbours' post-collision ones only, so across a cut only
+ * the populations that stream over it have to move, once per step: those
+ * with e_x = +1 (D2Q9: 3, D3Q19: 5) of a slab's last column go right, those
+ * with e_x = -1 of its first column go left.  The cycle per step, for every
+ * slab: vans_step(h, 1), vans_halo_pack, the exchange of the packed messages
+ * (a device copy on one GPU, a send/recv between GPUs; the caller's), then
+ * vans_halo_unpack.  A message holds vans_halo_floats(h) floats, laid out
+ * [k][row] with k the k-th direction (index order) of that x sign and row =
+ * z * ny + y.  The y and z walls are those of the whole domain. */
+
+/* Floats of one halo message of this handle, or -1 for a batch or NULL. */
+long long vans_halo_floats(vans_t h);
+
+/* vans_set_eps for a slab: eps_dev is the slab's own field (dense, its nx
+ * columns), eps_left and eps_right the porosity of the column just left of
+ * the slab and just right of it (the neighbouring slabs' edge columns; dense,
+ * ny * nz floats each, row = z * ny + y), which the slab's edge cells read
+ * for grad eps (Eq. pi) and for the populations they send across.  All
+ * values must lie in (0, 1], else VANS_ERR_ARG and nothing changes.  The
+ * handle then steps one step per vans_step call (VANS_ERR_UNSUPPORTED for
+ * nsteps > 1, for vans_step_monitored, vans_update_eps and the reverse
+ * pass) until the next vans_set_eps.  Synchronises. */
+int vans_set_eps_slab(vans_t h, const float *eps_dev, const float *eps_left,
+                      const float *eps_right);
+
+/* The messages of the current state: to_left gets the first column's
+ * populations with e_x = -1, to_right the last column's with e_x = +1
+ * (vans_halo_floats(h) floats each, distinct device buffers). */
+int vans_halo_pack(vans_t h, float *to_left, float *to_right);
+
+/* Write the neighbours' messages into the current state: from_left is the
+ * left neighbour's to_right, from_right the right neighbour's to_left.  A
+ * single slab that is its own neighbour (from_left = its to_right) gets the
+ * same state as the periodic wrap of vans_step. */
+int vans_halo_unpack(vans_t h, const float *from_left, const float *from_right);
 
 /* ---------------------------------------------------------------- misc --- */
 
@@ -329,7 +381,9 @@ long long vans_cells(vans_t h);
 long long vans_launch_count(vans_t h);
 
 /* Check the current state for non-finite values or |u| >= 0.5 (Mach ~0.9);
- * returns VANS_OK or VANS_ERR_DIVERGED.  Synchronises. */
+ * returns VANS_OK or VANS_ERR_DIVERGED, VANS_ERR_TIMEOUT if a bounded device
+ * wait of a step kernel gave up, VANS_ERR_ARG if the field of the last
+ * vans_set_eps_async was out of range.  Synchronises. */
 int vans_check(vans_t h);
 
 const char *vans_status_string(int status);

@@ -91,13 +91,13 @@ class Params:
 @dataclass
 class Launch:
     """``vans_launch`` (see include/vans.h).  kind 0: register-load kernel (cpt
-    cells per lane, warps x rows per block); kind 1: bulk-copy pipeline
-    (32*warps threads, cpt cells per thread per tile, rows = pipeline stages);
-    kind 2: pipeline over row strips with a porosity ring; kind 3: kind 2 with
-    consecutive cells per thread; kinds 4, 5: kinds 2, 3 with a producer warp
-    and per-warp stage release; kinds 6, 7: persistent CTAs over interleaved
-    row tiles.  ctas: at most that many CTAs per SM for kinds 1-7 (0: as many
-    as fit)."""
+    cells per lane, warps x rows per block); kind 2: bulk-copy pipeline over
+    row strips with a porosity ring (32*warps threads, cpt cells per thread per
+    tile, rows = pipeline stages); kinds 4, 5: kind 2 with a producer warp and
+    per-warp stage release (5: consecutive cells per thread); kinds 6, 7:
+    persistent CTAs over interleaved row tiles.  Kinds 1 and 3 are not built.
+    ctas: at most that many CTAs per SM for the pipelined kinds (0: as many as
+    fit)."""
     cpt: int
     warps: int
     rows: int
@@ -132,6 +132,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
                                            ctypes.POINTER(_H)]),
             "vans_destroy": (None, [_H]),
             "vans_set_eps": (ctypes.c_int, [_H, _F]),
+            "vans_set_eps_async": (ctypes.c_int, [_H, _F]),
             "vans_update_eps": (ctypes.c_int, [_H, _F]),
             "vans_step": (ctypes.c_int, [_H, ctypes.c_int]),
             "vans_step_raw": (ctypes.c_int, [_H, _F, _F]),
@@ -163,6 +164,10 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
                                                        ctypes.POINTER(ctypes.c_longlong)]),
             "vans_batch_cells": (ctypes.c_longlong, [_H]),
             "vans_cells": (ctypes.c_longlong, [_H]),
+            "vans_halo_floats": (ctypes.c_longlong, [_H]),
+            "vans_set_eps_slab": (ctypes.c_int, [_H, _F, _F, _F]),
+            "vans_halo_pack": (ctypes.c_int, [_H, _F, _F]),
+            "vans_halo_unpack": (ctypes.c_int, [_H, _F, _F]),
             "vans_launch_count": (ctypes.c_longlong, [_H]),
             "vans_check": (ctypes.c_int, [_H]),
             "vans_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -248,6 +253,86 @@ class Solver:
     # -- forward ----------------------------------------------------------
     def set_eps(self, eps):
         _check(self.lib.vans_set_eps(self._h, _f32(eps, self.params.cells, "eps")), "vans_set_eps")
+
+    def set_eps_async(self, eps):
+        """``vans_set_eps`` without the stream synchronisation: an out-of-range
+        field leaves the state undefined and makes the next ``check()`` fail."""
+        _check(self.lib.vans_set_eps_async(self._h, _f32(eps, self.params.cells, "eps")),
+               "vans_set_eps_async")
+
+    def run_jobs(self, eps_host, nsteps: int, rho_host, u_host):
+        """Jobs back to back, each one porosity field: its upload from pinned
+        host memory, ``vans_set_eps_async`` (rest state), ``nsteps`` steps,
+        ``vans_moments``, and rho and u back into pinned host memory.  The
+        copies run on a second stream and overlap the steps of the neighbouring
+        jobs (two device buffers of each kind take turns).  eps_host: pinned
+        float32 CPU tensors of N values; rho_host, u_host: pinned float32 CPU
+        tensors of N and D*N values that receive each job's results.  Returns
+        when the last results are on the host."""
+        torch = _torch()
+        p = self.params
+        n = len(eps_host)
+        if len(rho_host) != n or len(u_host) != n:
+            raise ValueError("one rho and one u buffer per job")
+        for t in list(eps_host) + list(rho_host) + list(u_host):
+            if t.is_cuda or not t.is_pinned() or t.dtype != torch.float32:
+                raise ValueError("host buffers must be pinned float32 CPU tensors")
+        dev = self.device
+        copy = torch.cuda.Stream(device=dev)
+        eps_d = [torch.empty(p.cells, dtype=torch.float32, device=dev) for _ in range(2)]
+        rho_d = [torch.empty(p.cells, dtype=torch.float32, device=dev) for _ in range(2)]
+        u_d = [torch.empty(p.dim * p.cells, dtype=torch.float32, device=dev) for _ in range(2)]
+        ev = lambda: torch.cuda.Event()  # noqa: E731
+        up, used, done, down = ([ev() for _ in range(n)] for _ in range(4))
+        with torch.cuda.stream(copy):
+            copy.wait_stream(self.stream)          # buffers allocated on the solver's stream
+            for k in range(min(2, n)):
+                eps_d[k].copy_(eps_host[k], non_blocking=True)
+                up[k].record(copy)
+        for k in range(n):
+            b = k % 2
+            self.stream.wait_event(up[k])
+            self.set_eps_async(eps_d[b])
+            used[k].record(self.stream)            # eps_d[b] has been read
+            self.step(nsteps)
+            if k >= 2:
+                self.stream.wait_event(down[k - 2])   # rho_d[b], u_d[b] are free again
+            self.moments(rho_d[b], u_d[b])
+            done[k].record(self.stream)
+            with torch.cuda.stream(copy):
+                copy.wait_event(done[k])
+                rho_host[k].copy_(rho_d[b], non_blocking=True)
+                u_host[k].copy_(u_d[b], non_blocking=True)
+                down[k].record(copy)
+                if k + 2 < n:
+                    copy.wait_event(used[k])
+                    eps_d[b].copy_(eps_host[k + 2], non_blocking=True)
+                    up[k + 2].record(copy)
+        copy.synchronize()
+        self.stream.synchronize()
+
+    # -- slabs along x -----------------------------------------------------
+    @property
+    def halo_floats(self) -> int:
+        return int(self.lib.vans_halo_floats(self._h))
+
+    def set_eps_slab(self, eps, eps_left, eps_right):
+        """The slab's own porosity field and the columns just left and right of
+        it (ny * nz values each)."""
+        rows = self.params.ny * self.params.nz
+        _check(self.lib.vans_set_eps_slab(self._h, _f32(eps, self.params.cells, "eps"),
+                                          _f32(eps_left, rows, "eps_left"),
+                                          _f32(eps_right, rows, "eps_right")), "vans_set_eps_slab")
+
+    def halo_pack(self, to_left, to_right):
+        n = self.halo_floats
+        _check(self.lib.vans_halo_pack(self._h, _f32(to_left, n, "to_left"),
+                                       _f32(to_right, n, "to_right")), "vans_halo_pack")
+
+    def halo_unpack(self, from_left, from_right):
+        n = self.halo_floats
+        _check(self.lib.vans_halo_unpack(self._h, _f32(from_left, n, "from_left"),
+                                         _f32(from_right, n, "from_right")), "vans_halo_unpack")
 
     def update_eps(self, eps):
         """New porosity field, same physical populations (eps varying in time)."""

@@ -3,7 +3,10 @@
 Each .cu translation unit is compiled in parallel by nvcc for
 ``-gencode arch=compute_103a,code=sm_103a`` only, then linked into a shared
 library inside the package (``paper_1406_6438_gb300/_build/libvans.so``).
-No fast-math: the divisions and square roots stay IEEE-rounded.
+No fast-math flag.  The step's reciprocals and square roots are the hardware
+estimates refined by one Newton-Raphson step each (within about an ulp of the
+correctly rounded results); ``extra_flags=("-DVANS_IEEE_MATH",)`` builds the
+correctly rounded variant, ``("-DVANS_RAW_ESTIMATES",)`` the unrefined one.
 """
 from __future__ import annotations
 

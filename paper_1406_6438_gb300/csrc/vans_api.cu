@@ -21,13 +21,18 @@ using vans::VDom;
 
 namespace {
 
-constexpr int kGraphSteps = 64;   // steps per captured graph (even: parity is restored)
+// Step sequences are replayed from captured CUDA graphs of 64, 32, ..., 2
+// steps (even lengths restore the buffer parity): a run of n steps is the
+// binary decomposition of n, so even short runs leave the per-launch overhead
+// of single launches behind (about 3 us of a 200 us step on GB300).
+constexpr int kGraphSizes = 6;
+constexpr int kGraphSteps = 64;   // the longest graph; size k holds kGraphSteps >> k steps
 
 long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
 
-int pitch_for(int nx) { return (int)round_up(VANS_OFF + round_up(nx, 128) + 1, 32); }
-
 // floats of one state buffer (Q planes of rows*pitch), rounded to 256 bytes
+using vans::pitch_for;
+
 long long state_floats_of(int q, int nx, int ny, int nz) {
     const long long plane = (long long)ny * nz * pitch_for(nx);
     return round_up((long long)q * plane, 64);
@@ -72,6 +77,38 @@ int validate(const vans_params *p, bool batched) {
     return VANS_OK;
 }
 
+bool launch_ok(const vans_launch *c, int q, bool batched) {
+    if (!c) return false;
+    if (c->cpt != 1 && c->cpt != 2 && c->cpt != 4) return false;
+    if (c->ctas < 0 || c->ctas > 4) return false;
+    if (c->kind == 0) {
+        if (c->ctas != 0) return false;
+        if (c->warps < 1 || c->warps > 8 || c->rows < 1 || c->rows > 8) return false;
+        return c->warps * c->rows <= 8;
+    }
+    // kinds 1 and 3 are not built (never the fastest at any measured size)
+    if (c->kind < 2 || c->kind > 7 || c->kind == 3) return false;
+    if (c->rows < 2 || c->rows > 6) return false;
+    // the instantiated pipeline shapes
+    const int nt = 32 * c->warps;
+    if (c->kind == 5 || c->kind == 7)
+        return (nt == 64 || nt == 128) && c->cpt == (q == 9 ? 4 : 2) && (q == 9 || !batched);
+    if (c->kind == 6)
+        return q == 9 ? (c->cpt == 2 && (nt == 128 || nt == 256))
+                      : (c->cpt == 1 && (nt == 128 || nt == 256) && !batched);
+    if (q == 9)
+        return (nt == 128 && (c->cpt == 2 || c->cpt == 4)) || (nt == 256 && c->cpt <= 2);
+    return (nt == 128 && c->cpt <= 2) || (nt == 256 && c->cpt == 1);
+}
+
+}  // namespace
+
+namespace vans {
+
+int pitch_for(int nx) {
+    return (int)((VANS_OFF + ((long long)nx + 127) / 128 * 128 + 1 + 31) / 32 * 32);
+}
+
 // Host-side constants of the drag law: alpha = ca * a(eps), beta = cb * b(eps).
 void fill_dom(const vans_params *p, VDom &d) {
     memset(&d, 0, sizeof(d));
@@ -112,30 +149,7 @@ void fill_dom(const vans_params *p, VDom &d) {
     d.moving = (!d.nee && (d.uw[0] != 0.f || d.uw[1] != 0.f || d.uw[2] != 0.f)) ? 1 : 0;
 }
 
-bool launch_ok(const vans_launch *c, int q, bool batched) {
-    if (!c) return false;
-    if (c->cpt != 1 && c->cpt != 2 && c->cpt != 4) return false;
-    if (c->ctas < 0 || c->ctas > 4) return false;
-    if (c->kind == 0) {
-        if (c->ctas != 0) return false;
-        if (c->warps < 1 || c->warps > 8 || c->rows < 1 || c->rows > 8) return false;
-        return c->warps * c->rows <= 8;
-    }
-    if (c->kind < 1 || c->kind > 7 || (batched && (c->kind == 1 || c->kind == 3))) return false;
-    if (c->rows < 2 || c->rows > 6) return false;
-    // the instantiated pipeline shapes
-    const int nt = 32 * c->warps;
-    if (c->kind == 3 || c->kind == 5 || c->kind == 7)
-        return (nt == 64 || nt == 128) && c->cpt == (q == 9 ? 4 : 2) && (q == 9 || !batched);
-    if (c->kind == 6)
-        return q == 9 ? (c->cpt == 2 && (nt == 128 || nt == 256))
-                      : (c->cpt == 1 && (nt == 128 || nt == 256) && !batched);
-    if (q == 9)
-        return (nt == 128 && (c->cpt == 2 || c->cpt == 4)) || (nt == 256 && c->cpt <= 2);
-    return (nt == 128 && c->cpt <= 2) || (nt == 256 && c->cpt == 1);
-}
-
-}  // namespace
+}  // namespace vans
 
 struct vans_s {
     bool batched = false;
@@ -145,7 +159,7 @@ struct vans_s {
     int device = 0;
     long long launches = 0;
     Launch L{4, 4, 1, 0};
-    cudaGraphExec_t gexec = nullptr;
+    cudaGraphExec_t gexec[kGraphSizes] = {};   // 64, 32, ..., 2 steps
     int *flag = nullptr;                        // device status words (workspace)
     int adj_fp64 = 0;                           // reverse-step arithmetic in FP64
     Launch adjL{1, 4, 4, 1};                    // reverse-step launch shape
@@ -156,6 +170,7 @@ struct vans_s {
     int cur = 0;
     float *eps_pad = nullptr;
     bool eps_set = false;
+    bool slab = false;                          // x halos come from neighbouring slabs
     long long sfloats = 0;
     // batched
     int n = 0;
@@ -183,9 +198,9 @@ namespace {
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? VANS_OK : VANS_ERR_CUDA; }
 
 void drop_graph(vans_t h) {
-    if (h->gexec) {
-        cudaGraphExecDestroy(h->gexec);
-        h->gexec = nullptr;
+    for (auto &g : h->gexec) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
     }
     for (auto &g : h->seg_graphs) cudaGraphExecDestroy(g.exec);
     h->seg_graphs.clear();
@@ -206,25 +221,39 @@ cudaError_t one_step(vans_t h, cudaStream_t s, int par) {
     return vans::launch_step(h->q, h->dom, h->st[par], h->st[par ^ 1], h->L, s);
 }
 
-int ensure_graph(vans_t h) {
-    if (h->gexec) return VANS_OK;
+// capture the graph of n steps starting at parity 0
+int capture_steps(vans_t h, int n, cudaGraphExec_t *out) {
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return VANS_ERR_CUDA;
     const long long before = h->launches;
     cudaError_t le = cudaSuccess;
-    for (int s = 0; s < kGraphSteps && le == cudaSuccess; ++s) le = one_step(h, h->cap, s & 1);
+    for (int s = 0; s < n && le == cudaSuccess; ++s) le = one_step(h, h->cap, s & 1);
     h->launches = before;                       // capture does not run anything
     e = cudaStreamEndCapture(h->cap, &g);
     if (le != cudaSuccess || e != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
         return VANS_ERR_CUDA;
     }
-    e = cudaGraphInstantiate(&h->gexec, g, 0);
+    e = cudaGraphInstantiate(out, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
-        h->gexec = nullptr;
+        *out = nullptr;
         return VANS_ERR_CUDA;
+    }
+    return VANS_OK;
+}
+
+// all graph sizes at once, so the first run that needs any of them pays the
+// capture for every later run length
+int ensure_graph(vans_t h) {
+    if (h->gexec[0]) return VANS_OK;
+    for (int k = 0; k < kGraphSizes; ++k) {
+        const int rc = capture_steps(h, kGraphSteps >> k, &h->gexec[k]);
+        if (rc) {
+            drop_graph(h);
+            return rc;
+        }
     }
     return VANS_OK;
 }
@@ -233,19 +262,22 @@ int ensure_graph(vans_t h) {
 int run_steps(vans_t h, int nsteps) {
     int &par = h->batched ? h->parity : h->cur;
     int left = nsteps;
-    if (left >= kGraphSteps) {
+    if (left >= 2) {
         if (par != 0) {
             if (one_step(h, h->stream, par) != cudaSuccess) return VANS_ERR_CUDA;
             par ^= 1;
             --left;
         }
-        if (left >= kGraphSteps) {
+        if (left >= 2) {
             int rc = ensure_graph(h);
             if (rc) return rc;
-            while (left >= kGraphSteps) {
-                if (cudaGraphLaunch(h->gexec, h->stream) != cudaSuccess) return VANS_ERR_CUDA;
-                h->launches += kGraphSteps;
-                left -= kGraphSteps;
+            for (int k = 0; k < kGraphSizes; ++k) {
+                const int n = kGraphSteps >> k;
+                while (left >= n) {
+                    if (cudaGraphLaunch(h->gexec[k], h->stream) != cudaSuccess) return VANS_ERR_CUDA;
+                    h->launches += n;
+                    left -= n;
+                }
             }
         }
     }
@@ -265,14 +297,34 @@ int make_streams(vans_t h, void *stream) {
 }
 
 // read the status words (flag[0]: range / divergence, flag[1]: a bounded
-// wait in a kernel timed out); synchronises the stream
-int read_flag(vans_t h, int *value, int *timeout = nullptr) {
-    int v[2] = {0, 0};
-    if (cudaMemcpyAsync(v, h->flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+// wait in a kernel timed out, flag[2]: the porosity of the last
+// vans_set_eps_async was out of range); synchronises the stream
+int read_flag(vans_t h, int *value, int *timeout = nullptr, int *eps_bad = nullptr) {
+    int v[3] = {0, 0, 0};
+    if (cudaMemcpyAsync(v, h->flag, 3 * sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
         return VANS_ERR_CUDA;
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return VANS_ERR_CUDA;
     *value = v[0];
     if (timeout) *timeout = v[1];
+    if (eps_bad) *eps_bad = v[2];
+    return VANS_OK;
+}
+
+// The rest state after a new porosity: the current buffer all zeros (the
+// deviations of f = w eps), plus the moving wall's gain.  The other buffer is
+// written whole (every cell and halo column) by the next step before anything
+// reads it, and its row padding is never read into a stored value.
+int reset_to_rest(vans_t h) {
+    if (cudaMemsetAsync(h->st[0], 0, h->sfloats * sizeof(float), h->stream) != cudaSuccess)
+        return VANS_ERR_CUDA;
+    if (h->dom.moving) {
+        ++h->launches;
+        if (vans::launch_init_moving(h->q, h->dom, h->st[0], h->stream) != cudaSuccess)
+            return VANS_ERR_CUDA;
+    }
+    h->cur = 0;
+    h->eps_set = true;
+    h->slab = false;
     return VANS_OK;
 }
 
@@ -399,25 +451,20 @@ std::vector<Launch> candidates(int q, bool batched) {
     }
     // bulk-copy pipeline shapes {cpt, warps, stages, kind}
     if (q == 9) {
-        const Launch t[] = {{2, 4, 3, 1}, {2, 4, 4, 1}, {4, 4, 2, 1}, {4, 4, 3, 1},
-                            {1, 8, 3, 1}, {1, 8, 4, 1}, {2, 8, 2, 1}, {2, 8, 3, 1},
-                            {2, 4, 3, 2}, {2, 4, 4, 2}, {4, 4, 3, 2}, {1, 8, 3, 2},
-                            {1, 8, 4, 2}, {2, 8, 3, 2}, {4, 4, 2, 3}, {4, 4, 3, 3},
-                            {4, 2, 3, 3}, {4, 2, 4, 3}, {2, 8, 2, 4}, {4, 4, 2, 4},
+        const Launch t[] = {{2, 4, 3, 2}, {2, 4, 4, 2}, {4, 4, 3, 2}, {1, 8, 3, 2},
+                            {1, 8, 4, 2}, {2, 8, 3, 2}, {2, 8, 2, 4}, {4, 4, 2, 4},
                             {4, 2, 2, 5}, {4, 4, 2, 5}, {4, 4, 4, 5}, {4, 4, 5, 5},
                             {4, 4, 6, 5}, {2, 8, 2, 6}, {2, 4, 2, 6}, {4, 4, 4, 7},
                             {4, 2, 4, 7}, {4, 4, 2, 7}, {4, 4, 2, 5, 2}, {4, 4, 3, 5, 2},
                             {4, 4, 2, 7, 2}, {4, 4, 3, 7, 2}, {4, 4, 2, 7, 3}};
         c.insert(c.end(), std::begin(t), std::end(t));
     } else {
-        const Launch t[] = {{1, 4, 3, 1}, {1, 4, 4, 1}, {2, 4, 2, 1}, {2, 4, 3, 1},
-                            {1, 8, 2, 1}, {1, 8, 3, 1}, {1, 4, 3, 2}, {2, 4, 2, 2},
-                            {2, 4, 3, 2}, {1, 8, 2, 2}, {1, 8, 3, 2}, {1, 4, 3, 4},
-                            {1, 8, 2, 4}, {2, 4, 2, 3}, {2, 4, 3, 3}, {2, 2, 3, 3},
-                            {2, 4, 2, 5}, {2, 4, 3, 5}, {2, 4, 4, 5}, {2, 2, 3, 5},
-                            {1, 4, 3, 6}, {1, 8, 3, 6}, {2, 4, 3, 7}, {2, 2, 3, 7},
-                            {2, 4, 2, 7}, {2, 4, 2, 7, 2}, {2, 4, 2, 7, 1}, {2, 4, 3, 7, 1},
-                            {2, 4, 3, 7, 2}, {2, 4, 2, 3, 2}, {2, 4, 2, 5, 2}};
+        const Launch t[] = {{1, 4, 3, 2}, {2, 4, 2, 2}, {2, 4, 3, 2}, {1, 8, 2, 2},
+                            {1, 8, 3, 2}, {1, 4, 3, 4}, {1, 8, 2, 4}, {2, 4, 2, 5},
+                            {2, 4, 3, 5}, {2, 4, 4, 5}, {2, 2, 3, 5}, {1, 4, 3, 6},
+                            {1, 8, 3, 6}, {2, 4, 3, 7}, {2, 2, 3, 7}, {2, 4, 2, 7},
+                            {2, 4, 2, 7, 2}, {2, 4, 2, 7, 1}, {2, 4, 3, 7, 1}, {2, 4, 3, 7, 2},
+                            {2, 4, 2, 5, 2}};
         c.insert(c.end(), std::begin(t), std::end(t));
     }
     return c;
@@ -452,7 +499,7 @@ int vans_create(const vans_params *p, void *workspace, size_t workspace_bytes, v
     if (!h) return VANS_ERR_ARG;
     h->q = p->q;
     h->p = *p;
-    fill_dom(p, h->dom);
+    vans::fill_dom(p, h->dom);
     h->sfloats = state_floats_of(p->q, p->nx, p->ny, p->nz);
     float *w = (float *)workspace;
     h->st[0] = w;
@@ -497,23 +544,26 @@ int vans_set_eps(vans_t h, const float *eps_dev) {
     if (rc) return rc;
     if (bad) return VANS_ERR_ARG;
     ++h->launches;
+    if (cudaMemsetAsync(h->flag + 2, 0, sizeof(int), h->stream) != cudaSuccess) return VANS_ERR_CUDA;
     if (vans::launch_pad_eps(h->dom, eps_dev, h->eps_pad, h->flag, h->stream) != cudaSuccess)
         return VANS_ERR_CUDA;
-    if (cudaMemsetAsync(h->st[0], 0, 2 * h->sfloats * sizeof(float), h->stream) != cudaSuccess)
+    return reset_to_rest(h);
+}
+
+int vans_set_eps_async(vans_t h, const float *eps_dev) {
+    if (!h || h->batched || !eps_dev) return VANS_ERR_ARG;
+    // one pass pads eps and flags any value outside (0, 1] in flag[2]
+    if (cudaMemsetAsync(h->flag + 2, 0, sizeof(int), h->stream) != cudaSuccess) return VANS_ERR_CUDA;
+    ++h->launches;
+    if (vans::launch_pad_eps(h->dom, eps_dev, h->eps_pad, h->flag + 2, h->stream) != cudaSuccess)
         return VANS_ERR_CUDA;
-    if (h->dom.moving) {
-        ++h->launches;
-        if (vans::launch_init_moving(h->q, h->dom, h->st[0], h->stream) != cudaSuccess)
-            return VANS_ERR_CUDA;
-    }
-    h->cur = 0;
-    h->eps_set = true;
-    return VANS_OK;
+    return reset_to_rest(h);
 }
 
 int vans_update_eps(vans_t h, const float *eps_dev) {
     if (!h || h->batched || !eps_dev) return VANS_ERR_ARG;
     if (!h->eps_set) return VANS_ERR_STATE;
+    if (h->slab) return VANS_ERR_UNSUPPORTED;
     if (cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream) != cudaSuccess) return VANS_ERR_CUDA;
     ++h->launches;
     if (vans::launch_pad_eps(h->dom, eps_dev, nullptr, h->flag, h->stream) != cudaSuccess)
@@ -533,6 +583,7 @@ int vans_update_eps(vans_t h, const float *eps_dev) {
 int vans_step(vans_t h, int nsteps) {
     if (!h || h->batched || nsteps < 0) return VANS_ERR_ARG;
     if (!h->eps_set) return VANS_ERR_STATE;
+    if (h->slab && nsteps > 1) return VANS_ERR_UNSUPPORTED;   // a halo exchange after each step
     return run_steps(h, nsteps);
 }
 
@@ -540,7 +591,7 @@ int vans_step_monitored(vans_t h, int nsteps, int every, float *rho_dev, float *
                         float *stats_dev) {
     if (!h || h->batched || nsteps < 0 || every < 1 || !rho_dev || !u_dev || !stats_dev)
         return VANS_ERR_ARG;
-    if (h->dom.nee) return VANS_ERR_UNSUPPORTED;    // plates on nodes: use vans_moments
+    if (h->dom.nee || h->slab) return VANS_ERR_UNSUPPORTED;    // plates on nodes: use vans_moments
     if (!h->eps_set) return VANS_ERR_STATE;
     if (cudaMemsetAsync(stats_dev, 0, 4 * sizeof(float), h->stream) != cudaSuccess)
         return VANS_ERR_CUDA;
@@ -672,7 +723,7 @@ int vans_flux(vans_t h, const float *state, int x_out, float *J_dev) {
 
 int vans_flux_seed(vans_t h, const float *state, int x_out, float *lam_dev, float *grad_acc) {
     if (!h || h->batched || !lam_dev || !grad_acc) return VANS_ERR_ARG;
-    if (h->dom.nee) return VANS_ERR_UNSUPPORTED;    // the adjoint covers bounce-back walls
+    if (h->dom.nee || h->slab) return VANS_ERR_UNSUPPORTED;    // the adjoint covers bounce-back walls
     if (!h->eps_set) return VANS_ERR_STATE;
     if (x_out < 0 || x_out >= h->dom.nx) return VANS_ERR_ARG;
     const int D = h->q == 9 ? 2 : 3;
@@ -690,7 +741,7 @@ int vans_step_adjoint(vans_t h, const float *state_t, const float *lam_in, float
                       float *grad_acc) {
     if (!h || h->batched || !state_t || !lam_in || !lam_out || !grad_acc) return VANS_ERR_ARG;
     if (lam_in == lam_out || (const float *)lam_out == state_t) return VANS_ERR_ARG;
-    if (h->dom.nee) return VANS_ERR_UNSUPPORTED;
+    if (h->dom.nee || h->slab) return VANS_ERR_UNSUPPORTED;
     if (!h->eps_set) return VANS_ERR_STATE;
     ++h->launches;
     return cuda_status(vans::launch_step_adjoint(h->q, h->dom, state_t, lam_in, lam_out, grad_acc,
@@ -700,7 +751,7 @@ int vans_step_adjoint(vans_t h, const float *state_t, const float *lam_in, float
 int vans_adjoint_segment(vans_t h, const float *ckpt, float *seg, int len, float *lam, float *tmp,
                          float *grad_acc) {
     if (!h || h->batched || !ckpt || !seg || !lam || !tmp || !grad_acc || len < 1) return VANS_ERR_ARG;
-    if (h->dom.nee) return VANS_ERR_UNSUPPORTED;
+    if (h->dom.nee || h->slab) return VANS_ERR_UNSUPPORTED;
     if (lam == tmp) return VANS_ERR_ARG;
     if (!h->eps_set) return VANS_ERR_STATE;
     const long long sf = h->sfloats;
@@ -804,11 +855,56 @@ int vans_check(vans_t h) {
         if (vans::launch_check(h->q, h->dom, h->st[h->cur], h->flag, h->stream) != cudaSuccess)
             return VANS_ERR_CUDA;
     }
-    int bad = 0, tmo = 0;
-    int rc = read_flag(h, &bad, &tmo);
+    int bad = 0, tmo = 0, eps_bad = 0;
+    int rc = read_flag(h, &bad, &tmo, &eps_bad);
     if (rc) return rc;
     if (tmo) return VANS_ERR_TIMEOUT;
+    if (eps_bad) return VANS_ERR_ARG;
     return bad ? VANS_ERR_DIVERGED : VANS_OK;
+}
+
+long long vans_halo_floats(vans_t h) {
+    if (!h || h->batched) return -1;
+    return vans::halo_floats(h->q, h->dom);
+}
+
+int vans_set_eps_slab(vans_t h, const float *eps_dev, const float *eps_left,
+                      const float *eps_right) {
+    if (!h || h->batched || !eps_dev || !eps_left || !eps_right) return VANS_ERR_ARG;
+    // the halo columns first (check only), then the slab's own field
+    if (cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream) != cudaSuccess) return VANS_ERR_CUDA;
+    ++h->launches;
+    if (vans::launch_eps_halo(h->dom, eps_left, eps_right, nullptr, h->flag, h->stream) !=
+        cudaSuccess)
+        return VANS_ERR_CUDA;
+    int bad = 0;
+    int rc = read_flag(h, &bad);
+    if (rc) return rc;
+    if (bad) return VANS_ERR_ARG;
+    rc = vans_set_eps(h, eps_dev);
+    if (rc) return rc;
+    ++h->launches;
+    if (vans::launch_eps_halo(h->dom, eps_left, eps_right, h->eps_pad, h->flag, h->stream) !=
+        cudaSuccess)
+        return VANS_ERR_CUDA;
+    h->slab = true;
+    return VANS_OK;
+}
+
+int vans_halo_pack(vans_t h, float *to_left, float *to_right) {
+    if (!h || h->batched || !to_left || !to_right || to_left == to_right) return VANS_ERR_ARG;
+    if (!h->eps_set) return VANS_ERR_STATE;
+    ++h->launches;
+    return cuda_status(
+        vans::launch_halo_pack(h->q, h->dom, h->st[h->cur], to_left, to_right, h->stream));
+}
+
+int vans_halo_unpack(vans_t h, const float *from_left, const float *from_right) {
+    if (!h || h->batched || !from_left || !from_right) return VANS_ERR_ARG;
+    if (!h->eps_set) return VANS_ERR_STATE;
+    ++h->launches;
+    return cuda_status(
+        vans::launch_halo_unpack(h->q, h->dom, h->st[h->cur], from_left, from_right, h->stream));
 }
 
 long long vans_cells(vans_t h) {
@@ -868,7 +964,7 @@ int vans_batch_create(const vans_params *p, int n, void *workspace, size_t works
     long long dense = 0;
     for (int d = 0; d < n; ++d) {
         VDom &D = h->doms[d];
-        fill_dom(&p[d], D);
+        vans::fill_dom(&p[d], D);
         const long long sf = state_floats_of(9, p[d].nx, p[d].ny, 1);
         D.f[0] = (float *)w;
         D.f[1] = (float *)w + sf;

@@ -478,6 +478,84 @@ __global__ void k_grad_finalize(const VDom d, const float *__restrict__ lam0,
 }
 
 // --------------------------------------------------------------- launch ---
+// ------------------------------------------------------ slabs along x ----
+// A domain cut along x into slabs: the pull of a slab's column 0 reads the
+// halo column -1 for the directions with e_x = +1, and that of its last column
+// reads column nx for e_x = -1.  These entries belong to the neighbouring
+// slabs' edge cells, so after every step each slab sends its last column's
+// e_x = +1 entries to the right and its first column's e_x = -1 entries to
+// the left.  A message is [k][row], k the k-th direction with e_x = +1 (resp.
+// -1) in index order, row = z * ny + y.
+
+// the k-th direction (index order) whose x component is sx
+template <int Q>
+__host__ __device__ constexpr int xdir(int sx, int k) {
+    for (int i = 0, n = 0; i < Q; ++i)
+        if (Lat<Q>::ex(i) == sx && n++ == k) return i;
+    return -1;
+}
+
+template <int Q>
+__host__ __device__ constexpr int n_xdirs() {
+    int n = 0;
+    for (int i = 0; i < Q; ++i) n += Lat<Q>::ex(i) == 1;
+    return n;
+}
+
+template <int Q>
+__global__ void k_halo_pack(const VDom d, const float *__restrict__ st, float *__restrict__ to_left,
+                            float *__restrict__ to_right) {
+    constexpr int NX = n_xdirs<Q>();
+    const long long total = (long long)d.rows * NX;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(t / d.rows);
+        const long long r = t - (long long)k * d.rows;
+        const long long ro = r * d.pitch + VANS_OFF;
+        int ip = 0, im = 0;
+#pragma unroll
+        for (int j = 0; j < NX; ++j)
+            if (j == k) { ip = xdir<Q>(1, j); im = xdir<Q>(-1, j); }
+        to_right[t] = st[ip * d.plane + ro + d.nx - 1];
+        to_left[t] = st[im * d.plane + ro];
+    }
+}
+
+template <int Q>
+__global__ void k_halo_unpack(const VDom d, float *__restrict__ st, const float *__restrict__ from_left,
+                              const float *__restrict__ from_right) {
+    constexpr int NX = n_xdirs<Q>();
+    const long long total = (long long)d.rows * NX;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(t / d.rows);
+        const long long r = t - (long long)k * d.rows;
+        const long long ro = r * d.pitch + VANS_OFF;
+        int ip = 0, im = 0;
+#pragma unroll
+        for (int j = 0; j < NX; ++j)
+            if (j == k) { ip = xdir<Q>(1, j); im = xdir<Q>(-1, j); }
+        st[ip * d.plane + ro - 1] = from_left[t];
+        st[im * d.plane + ro + d.nx] = from_right[t];
+    }
+}
+
+// The porosity halo columns of a slab: column -1 from the left neighbour's
+// last column, column nx from the right neighbour's first (dense, one value
+// per row).  Values outside (0, 1] set *flag; pad == nullptr checks only.
+__global__ void k_eps_halo(const VDom d, const float *__restrict__ left,
+                           const float *__restrict__ right, float *__restrict__ pad, int *flag) {
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < d.rows;
+         r += (long long)gridDim.x * blockDim.x) {
+        const float a = left[r], b = right[r];
+        if (!(a > 0.0f && a <= 1.0f) || !(b > 0.0f && b <= 1.0f)) atomicOr(flag, 1);
+        if (pad) {
+            pad[r * d.pitch + VANS_OFF - 1] = a;
+            pad[r * d.pitch + VANS_OFF + d.nx] = b;
+        }
+    }
+}
+
 static int grid_for(long long n, int threads) {
     long long b = (n + threads - 1) / threads;
     if (b > 152 * 64) b = 152 * 64;
@@ -599,6 +677,32 @@ cudaError_t launch_grad_finalize(int q, const VDom &d, const float *lam0, const 
     const int g = grid_for(d.cells, 256);
     VANS_DISPATCH_Q(q, (k_grad_finalize<9><<<g, 256, 0, s>>>(d, lam0, grad, dJ)),
                     (k_grad_finalize<19><<<g, 256, 0, s>>>(d, lam0, grad, dJ)));
+    return cudaGetLastError();
+}
+
+int halo_floats(int q, const VDom &d) {
+    return (int)((q == 9 ? n_xdirs<9>() : n_xdirs<19>()) * (long long)d.rows);
+}
+
+cudaError_t launch_halo_pack(int q, const VDom &d, const float *state, float *to_left,
+                             float *to_right, cudaStream_t s) {
+    const int g = grid_for(halo_floats(q, d), 256);
+    VANS_DISPATCH_Q(q, (k_halo_pack<9><<<g, 256, 0, s>>>(d, state, to_left, to_right)),
+                    (k_halo_pack<19><<<g, 256, 0, s>>>(d, state, to_left, to_right)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_halo_unpack(int q, const VDom &d, float *state, const float *from_left,
+                               const float *from_right, cudaStream_t s) {
+    const int g = grid_for(halo_floats(q, d), 256);
+    VANS_DISPATCH_Q(q, (k_halo_unpack<9><<<g, 256, 0, s>>>(d, state, from_left, from_right)),
+                    (k_halo_unpack<19><<<g, 256, 0, s>>>(d, state, from_left, from_right)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eps_halo(const VDom &d, const float *left, const float *right, float *eps_pad,
+                            int *flag, cudaStream_t s) {
+    k_eps_halo<<<grid_for(d.rows, 256), 256, 0, s>>>(d, left, right, eps_pad, flag);
     return cudaGetLastError();
 }
 

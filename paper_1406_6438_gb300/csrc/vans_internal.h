@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "vans.h"
+
 #define VANS_OFF 8  // column 0 of a padded row sits 8 floats (one 32-byte sector) into the row
 
 namespace vans {
@@ -44,13 +46,22 @@ struct Tile {
 };
 
 // kind 0: register-load kernel k_step (cpt cells per lane, warps x rows per block)
-// kind 1: bulk-copy pipeline k_step_tma (32*warps threads, cpt cells per thread
-//         per tile, rows = pipeline stages)
-// ctas: at most that many CTAs per SM for kinds 1-7 (0: as many as fit)
+// kinds 2, 4-7: bulk-copy pipelines (32*warps compute threads, cpt cells per
+//         thread per tile, rows = pipeline stages)
+// ctas: at most that many CTAs per SM for the pipelined kinds (0: as many as fit)
 struct Launch {
     int cpt, warps, rows, kind;
     int ctas;
 };
+
+// ------------------------------------------------------- host helpers ----
+// Floats per padded row for a row of nx cells: column 0 at float VANS_OFF,
+// columns -1 and nx as halo copies, rounded up to whole 128-byte lines.
+int pitch_for(int nx);
+// The kernel descriptor of one domain from validated parameters: sizes, row
+// layout, relaxation and drag constants, walls.  Buffers (eps, f, status) are
+// left null for the caller to set.
+void fill_dom(const vans_params *p, VDom &d);
 
 // ------------------------------------------------------ kernel launchers ----
 // Each returns cudaSuccess or the launch error.  `stream` is where they enqueue.
@@ -93,5 +104,14 @@ cudaError_t launch_step_adjoint(int q, const VDom &d, const float *state, const 
                                 cudaStream_t stream);
 cudaError_t launch_grad_finalize(int q, const VDom &d, const float *lam0, const float *grad,
                                  float *dJ, cudaStream_t stream);
+// slabs along x: floats of one halo message, pack / unpack of the edge
+// columns' crossing populations, the porosity halo columns
+int halo_floats(int q, const VDom &d);
+cudaError_t launch_halo_pack(int q, const VDom &d, const float *state, float *to_left,
+                             float *to_right, cudaStream_t stream);
+cudaError_t launch_halo_unpack(int q, const VDom &d, float *state, const float *from_left,
+                               const float *from_right, cudaStream_t stream);
+cudaError_t launch_eps_halo(const VDom &d, const float *left, const float *right, float *eps_pad,
+                            int *flag, cudaStream_t stream);
 
 }  // namespace vans

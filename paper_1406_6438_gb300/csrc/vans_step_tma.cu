@@ -11,19 +11,22 @@
 // flight).  Shared-memory reads are unit-stride across a warp and the +-1
 // column shift of the pull is an offset.  The launch kinds of this file:
 //
-//   1  k_step_tma: persistent CTAs over contiguous runs of tiles, porosity
-//      rows staged per tile; a block barrier before each refill.
 //   2  k_step_tma_ring: each CTA walks a strip of consecutive rows of one
 //      column block and keeps the porosity rows in a shared-memory ring (each
-//      row leaves HBM once per strip).
-//   3  kind 2 with each thread on V adjacent cells (16- or 8-byte shared loads
-//      and global stores).
-//   4, 5  kinds 2, 3 warp-specialised: a producer warp refills a stage when
-//      every compute warp has released it on an "empty" mbarrier, which each
-//      warp does right after reading the stage into registers.
+//      row leaves HBM once per strip); thread 0 refills a stage after a block
+//      barrier.
+//   4, 5  kind 2 warp-specialised: a producer warp refills a stage when every
+//      compute warp has released it on an "empty" mbarrier, which each warp
+//      does right after reading the stage into registers; 4 strided cells, 5
+//      each thread on V adjacent cells (16- or 8-byte shared loads and global
+//      stores).
 //   6, 7  k_step_tma_ilv: persistent CTAs take tiles b, b+G, ... of the
 //      row-major order (the whole grid sweeps one band of rows), warp-
 //      specialised as 4/5; 6 strided cells, 7 adjacent cells.
+//
+// (Kinds 1 -- a pipeline over contiguous runs of tiles with the porosity rows
+// staged per tile -- and 3 -- kind 2 with adjacent cells -- were never the
+// fastest at any measured size and are not built.)
 //
 // The batched step (kinds 2, 4-7 over many domains) uses the same tile bodies
 // with a strip table or an interleaved tile table; plates-on-nodes instances
@@ -32,110 +35,6 @@
 
 namespace vans {
 
-
-template <int Q, int NT, int CPT>
-__global__ void __launch_bounds__(NT) k_step_tma(const VDom d, const float *__restrict__ fin,
-                                                 float *__restrict__ fout, int ntx, int ntiles,
-                                                 int stages) {
-    using L = Lat<Q>;
-    constexpr int TW = NT * CPT;
-    constexpr int SEG = TW + 2 * kLead;
-    constexpr int NS = Q + EpsRows<Q>::N;
-    extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
-    float *buf = reinterpret_cast<float *>(smem + kBarBytes);
-    const int tid = threadIdx.x;
-    const int t0 = (int)((long long)blockIdx.x * ntiles / gridDim.x);
-    const int t1 = (int)((long long)(blockIdx.x + 1) * ntiles / gridDim.x);
-    const int n = t1 - t0;
-    if (n <= 0) return;
-
-    if (tid == 0) {
-        for (int s = 0; s < stages; ++s) mbar_init(&bars[s], 1);
-        mbar_init_fence();
-    }
-    __syncthreads();
-    // tile cursors (row, column block) advanced one tile at a time: the
-    // consumer's for tile t0 + k, thread 0's producer one `stages` tiles ahead
-    int row = t0 / ntx, xt = t0 - (t0 / ntx) * ntx;
-    int prow = row, pxt = xt;
-    if (tid == 0) {
-        const int pre = n < stages ? n : stages;
-        for (int k = 0; k < pre; ++k) {
-            issue_tile<Q, TW>(d, fin, prow, pxt * TW, buf + k * (NS * SEG), &bars[k]);
-            if (++pxt == ntx) { pxt = 0; ++prow; }
-        }
-    }
-
-    int k = 0, s = 0;
-    uint32_t par = 0;
-    bool ok = true;
-    for (; k < n; ++k) {
-        ok = __syncthreads_and(mbar_wait_bounded(&bars[s], par));
-        if (!ok) break;
-        const float *sb = buf + s * (NS * SEG);
-        const int xs = xt * TW;
-        int y, z;
-        Nb3 Y, Z;
-        row_nbs<Q>(d, row, y, z, Y, Z);
-        const long long ro = row_offset(d, y, z);
-#pragma unroll
-        for (int c = 0; c < CPT; ++c) {
-            const int xl = tid + c * NT;
-            const int x = xs + xl;
-            float h[Q], et[Q], o[Q];
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const bool bb = Y.wall[1 - L::ey(i)] || Z.wall[1 - L::ez(i)];
-                h[i] = sb[i * SEG + kLead + xl + (bb ? 0 : -L::ex(i))];
-            }
-            const float e0 = sb[(Q + eps_slot<Q>(0, 0)) * SEG + kLead + xl];
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const bool wall = Y.wall[1 + L::ey(i)] || Z.wall[1 + L::ez(i)];
-                et[i] = (i == 0 || wall)
-                            ? e0
-                            : sb[(Q + eps_slot<Q>(L::ey(i), L::ez(i))) * SEG + kLead + xl + L::ex(i)];
-            }
-            apply_moving_wall<Q>(d, Y.wall[2], Z, e0, h);
-            collide<Q>(d, h, e0, et, o);
-            if (x < d.nx) {
-#pragma unroll
-                for (int i = 0; i < Q; ++i) fout[i * d.plane + ro + x] = o[i];
-                if (x == 0) {
-#pragma unroll
-                    for (int i = 0; i < Q; ++i)
-                        if (L::ex(i) < 0) store_halo_hi<Q>(fout + i * d.plane + ro, d.nx, o[i]);
-                }
-                if (x == d.nx - 1) {
-#pragma unroll
-                    for (int i = 0; i < Q; ++i)
-                        if (L::ex(i) > 0) store_halo_lo<Q>(fout + i * d.plane + ro, o[i]);
-                }
-            }
-        }
-        __syncthreads();                 // everyone is done reading stage s
-        if (tid == 0 && k + stages < n) {
-            fence_proxy_async_smem();
-            issue_tile<Q, TW>(d, fin, prow, pxt * TW, buf + s * (NS * SEG), &bars[s]);
-            if (++pxt == ntx) { pxt = 0; ++prow; }
-        }
-        if (++xt == ntx) { xt = 0; ++row; }
-        if (++s == stages) { s = 0; par ^= 1u; }
-    }
-    if (!ok) {
-        // a copy did not land within the time limit: flag it, then give the
-        // copies already issued into this CTA's shared memory a bounded chance
-        // to finish before the CTA exits
-        if (tid == 0) {
-            if (d.status) atomicOr(d.status, 2);
-            const int last = (k + stages < n) ? k + stages : n;
-            for (int j = k; j < last; ++j)
-                mbar_wait_bounded(&bars[j % stages], (uint32_t)((j / stages) & 1));
-        }
-        __syncthreads();
-    }
-}
 
 // ---------------------------------------------------------------------------
 // Variant with a porosity ring.  Each CTA walks one strip: a column block xt,
@@ -897,38 +796,6 @@ static cudaError_t launch_ring_t(const VDom &d, const float *fin, float *fout, i
     return cudaGetLastError();
 }
 
-template <int Q, int NT, int CPT>
-static size_t tma_smem_bytes(int stages) {
-    constexpr int TW = NT * CPT;
-    constexpr int NS = Q + EpsRows<Q>::N;
-    return kBarBytes + (size_t)stages * NS * (TW + 2 * kLead) * sizeof(float);
-}
-
-template <int Q, int NT, int CPT>
-static cudaError_t launch_tma_t(const VDom &d, const float *fin, float *fout, int stages, int ctas,
-                                cudaStream_t stream) {
-    constexpr int TW = NT * CPT;
-    const size_t smem = tma_smem_bytes<Q, NT, CPT>(stages);
-    if (stages < 2 || stages > 16 || smem > 227 * 1024) return cudaErrorInvalidValue;
-    const size_t smem_req = cap_smem(smem, ctas);
-    auto kern = k_step_tma<Q, NT, CPT>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_req);
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, occ = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem_req);
-    if (e != cudaSuccess) return e;
-    if (occ < 1) return cudaErrorInvalidConfiguration;
-    const int ntx = (d.nx + TW - 1) / TW;
-    const long long ntiles = (long long)ntx * d.rows;
-    if (ntiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    long long grid = (long long)sms * occ;
-    if (grid > ntiles) grid = ntiles;
-    kern<<<(unsigned)grid, NT, smem_req, stream>>>(d, fin, fout, ntx, (int)ntiles, stages);
-    return cudaGetLastError();
-}
-
 template <int NT, int CPT, bool VEC = false, bool WS = false>
 static cudaError_t launch_ring_batched_t(const VDom *doms, const Tile *strips, int nstrips, int parity,
                                          int stages, int ctas, cudaStream_t stream,
@@ -1015,9 +882,9 @@ cudaError_t launch_ring_batched(const VDom *doms, const Tile *strips, int nstrip
 }
 
 // L.warps -> compute threads per CTA (32 * warps), L.cpt -> cells per thread
-// per tile, L.rows -> pipeline stages; kind 1 the plain pipeline, 2 the
-// porosity ring, 3 the ring with contiguous cells (D2Q9), 4 and 5 the
-// warp-specialised forms of 2 and 3 (one extra producer warp)
+// per tile, L.rows -> pipeline stages; kind 2 the porosity ring, 4 and 5 its
+// warp-specialised forms (one extra producer warp; 5 with contiguous cells),
+// 6 and 7 the interleaved tiles.
 // The launch shapes with a plates-on-nodes instance (wall_kind 1).
 static bool plate_shape(int q, const Launch &L) {
     const int nt = 32 * L.warps;
@@ -1025,7 +892,7 @@ static bool plate_shape(int q, const Launch &L) {
         return (L.kind == 2 && nt == 128 && (L.cpt == 2 || L.cpt == 4)) ||
                ((L.kind == 5 || L.kind == 7) && L.cpt == 4 && (nt == 64 || nt == 128));
     return (L.kind == 2 && nt == 128 && L.cpt == 1) ||
-           ((L.kind == 3 || L.kind == 5 || L.kind == 7) && nt == 128 && L.cpt == 2);
+           ((L.kind == 5 || L.kind == 7) && nt == 128 && L.cpt == 2);
 }
 
 bool launch_has_plates(int q, Launch L) { return L.kind == 0 || plate_shape(q, L); }
@@ -1046,7 +913,6 @@ static cudaError_t launch_plates(int q, const VDom &d, const float *fin, float *
                         : launch_ilv_t<9, 128, 4, true, true>(d, fin, fout, st, L.ctas, stream);
     }
     if (L.kind == 2) return launch_ring_t<19, 128, 1, false, false, true>(d, fin, fout, st, L.ctas, stream);
-    if (L.kind == 3) return launch_ring_t<19, 128, 2, true, false, true>(d, fin, fout, st, L.ctas, stream);
     if (L.kind == 5) return launch_ring_t<19, 128, 2, true, true, true>(d, fin, fout, st, L.ctas, stream);
     return launch_ilv_t<19, 128, 2, true, true>(d, fin, fout, st, L.ctas, stream);
 }
@@ -1069,25 +935,15 @@ cudaError_t launch_step_tma(int q, const VDom &d, const float *fin, float *fout,
         if (q == 19 && nt == 128 && L.cpt == 2) return launch_ilv_t<19, 128, 2, true>(d, fin, fout, L.rows, L.ctas, stream);
         return cudaErrorInvalidValue;
     }
-    if (L.kind == 3 || L.kind == 5) {   // ring pipeline, consecutive cells per thread
-        const bool ws = L.kind == 5;
-        if (q == 19) {                  // 2 cells per thread
-            if (L.cpt != 2) return cudaErrorInvalidValue;
-            if (nt == 64)
-                return ws ? launch_ring_t<19, 64, 2, true, true>(d, fin, fout, L.rows, L.ctas, stream)
-                          : launch_ring_t<19, 64, 2, true>(d, fin, fout, L.rows, L.ctas, stream);
-            if (nt == 128)
-                return ws ? launch_ring_t<19, 128, 2, true, true>(d, fin, fout, L.rows, L.ctas, stream)
-                          : launch_ring_t<19, 128, 2, true>(d, fin, fout, L.rows, L.ctas, stream);
-            return cudaErrorInvalidValue;
+    if (L.kind == 5) {                  // warp-specialised ring, consecutive cells per thread
+        if (q == 19 && L.cpt == 2) {
+            if (nt == 64) return launch_ring_t<19, 64, 2, true, true>(d, fin, fout, L.rows, L.ctas, stream);
+            if (nt == 128) return launch_ring_t<19, 128, 2, true, true>(d, fin, fout, L.rows, L.ctas, stream);
         }
-        if (q != 9 || L.cpt != 4) return cudaErrorInvalidValue;
-        if (nt == 64)
-            return ws ? launch_ring_t<9, 64, 4, true, true>(d, fin, fout, L.rows, L.ctas, stream)
-                      : launch_ring_t<9, 64, 4, true>(d, fin, fout, L.rows, L.ctas, stream);
-        if (nt == 128)
-            return ws ? launch_ring_t<9, 128, 4, true, true>(d, fin, fout, L.rows, L.ctas, stream)
-                      : launch_ring_t<9, 128, 4, true>(d, fin, fout, L.rows, L.ctas, stream);
+        if (q == 9 && L.cpt == 4) {
+            if (nt == 64) return launch_ring_t<9, 64, 4, true, true>(d, fin, fout, L.rows, L.ctas, stream);
+            if (nt == 128) return launch_ring_t<9, 128, 4, true, true>(d, fin, fout, L.rows, L.ctas, stream);
+        }
         return cudaErrorInvalidValue;
     }
     if (L.kind == 2 || L.kind == 4) {
@@ -1106,17 +962,6 @@ cudaError_t launch_step_tma(int q, const VDom &d, const float *fin, float *fout,
 #undef VANS_RING_CASE
         return cudaErrorInvalidValue;
     }
-#define VANS_TMA_CASE(QQ, NTT, CC)                              \
-    if (q == QQ && nt == NTT && L.cpt == CC)                    \
-        return launch_tma_t<QQ, NTT, CC>(d, fin, fout, L.rows, L.ctas, stream);
-    VANS_TMA_CASE(9, 128, 2)
-    VANS_TMA_CASE(9, 128, 4)
-    VANS_TMA_CASE(9, 256, 1)
-    VANS_TMA_CASE(9, 256, 2)
-    VANS_TMA_CASE(19, 128, 1)
-    VANS_TMA_CASE(19, 128, 2)
-    VANS_TMA_CASE(19, 256, 1)
-#undef VANS_TMA_CASE
     return cudaErrorInvalidValue;
 }
 

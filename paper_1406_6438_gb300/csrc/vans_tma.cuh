@@ -49,14 +49,8 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
-// L2 eviction-priority policies for the copies' cache hints: rows that are read
-// once go first, rows that other CTAs read again soon (porosity) stay longest
-__device__ __forceinline__ uint64_t l2_evict_first() {
-    uint64_t p;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-
+// L2 eviction-priority policy for the copies' cache hint: rows that other
+// CTAs read again soon (porosity) stay longest
 __device__ __forceinline__ uint64_t l2_evict_last() {
     uint64_t p;
     asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));

@@ -20,18 +20,23 @@ def _autotuned(p, eps):
     return s
 
 
-def test_periodic_4096_every_cell_after_10_steps():
+def test_periodic_4096_every_cell_after_200_steps():
+    """The 4096^2 workload, 200 of its 1000 steps (the oracle takes about a
+    minute of host time for them), every population, rho and u against the
+    FP64 oracle."""
     torch = torch_cuda()
     p, eps, _ = W.periodic_2d(4096)
     s = _autotuned(p, eps)
-    s.step(10)
+    s.step(200)
     rho, u = s.moments()
     f = s.populations()
     torch.cuda.synchronize()
-    rho_o, u_o, f_o = oracle_run(p, eps, 10)
-    assert np.abs(f.cpu().numpy() - f_o).max() <= 2e-7
-    assert rel_u(u.cpu().numpy().astype(np.float64), u_o) <= 1e-5
-    assert np.abs(rho.cpu().numpy() - rho_o).max() <= 1e-6
+    rho_o, u_o, f_o = oracle_run(p, eps, 200)
+    err_f = float(np.abs(f.cpu().numpy() - f_o).max())
+    err_u = rel_u(u.cpu().numpy().astype(np.float64), u_o)
+    err_r = float(np.abs(rho.cpu().numpy() - rho_o).max())
+    print(f"4096^2 x 200: f {err_f:.2e}, u {err_u:.2e}, rho {err_r:.2e}, launch {s.launch}")
+    assert err_f <= 1e-6 and err_u <= 1e-5 and err_r <= 2e-6, (err_f, err_u, err_r)
 
 
 def test_periodic_4096_long_run_properties():
@@ -49,16 +54,22 @@ def test_periodic_4096_long_run_properties():
     assert abs(m1 - m0) <= 1e-6 * m0
 
 
-def test_duct_256cubed_every_cell_after_4_steps():
+def test_duct_256cubed_every_cell_after_50_steps():
+    """The 256^3 duct, 50 of its 500 steps, every population, rho and u against
+    the FP64 oracle."""
     torch = torch_cuda()
     p, eps, _ = W.duct_3d()
     s = _autotuned(p, eps)
-    s.step(4)
+    s.step(50)
     rho, u = s.moments()
+    f = s.populations()
     torch.cuda.synchronize()
-    rho_o, u_o, _ = oracle_run(p, eps, 4)
-    assert rel_u(u.cpu().numpy().astype(np.float64), u_o) <= 1e-5
-    assert np.abs(rho.cpu().numpy() - rho_o).max() <= 1e-6
+    rho_o, u_o, f_o = oracle_run(p, eps, 50)
+    err_f = float(np.abs(f.cpu().numpy() - f_o).max())
+    err_u = rel_u(u.cpu().numpy().astype(np.float64), u_o)
+    err_r = float(np.abs(rho.cpu().numpy() - rho_o).max())
+    print(f"256^3 x 50: f {err_f:.2e}, u {err_u:.2e}, rho {err_r:.2e}, launch {s.launch}")
+    assert err_f <= 1e-6 and err_u <= 1e-5 and err_r <= 2e-6, (err_f, err_u, err_r)
 
 
 def test_duct_256cubed_long_run_properties():
@@ -82,7 +93,7 @@ def test_duct_256cubed_long_run_properties():
 def test_batched_256_domains_sampled():
     """The 256-domain batch in its autotuned configuration: eight domains
     (the largest, the smallest and six drawn with a seed) against the oracle
-    after 30 steps; every domain finite after the workload's 2000 steps."""
+    after 300 steps; every domain finite after the workload's 2000 steps."""
     torch = torch_cuda()
     import paper_1406_6438_gb300 as V
     doms = W.batched_channels()
@@ -90,17 +101,17 @@ def test_batched_256_domains_sampled():
     for d, (_, e) in enumerate(doms):
         b.set_eps(d, torch.from_numpy(e).cuda().view(-1))
     b.autotune()
-    b.step(30)
+    b.step(300)
     torch.cuda.synchronize()
     sizes = [p["nx"] * p["ny"] for p, _ in doms]
     pick = {int(np.argmax(sizes)), int(np.argmin(sizes))}
     pick |= set(int(k) for k in np.random.default_rng(7).choice(len(doms), 6, replace=False))
     for d in sorted(pick):
         p, e = doms[d]
-        _, u_o, f_o = oracle_run(p, e, 30)
+        _, u_o, f_o = oracle_run(p, e, 300)
         f = b.populations(d).cpu().numpy()
         _, u = b.moments(d)
-        assert np.abs(f - f_o).max() <= 2e-7, d
+        assert np.abs(f - f_o).max() <= 1e-6, (d, np.abs(f - f_o).max())
         assert rel_u(u.cpu().numpy().astype(np.float64), u_o) <= 1e-5, d
-    b.step(2000 - 30)
+    b.step(2000 - 300)
     assert b.check()
