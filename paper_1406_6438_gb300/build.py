@@ -22,7 +22,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libvans.so")
 SOURCES = ["vans_step.cu", "vans_step_tma.cu", "vans_aux.cu", "vans_adjoint_tma.cu", "vans_api.cu",
-           "vans_static.cu"]
+           "vans_static.cu", "vans_cluster.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

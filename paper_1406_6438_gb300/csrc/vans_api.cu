@@ -86,6 +86,9 @@ bool launch_ok(const vans_launch *c, int q, bool batched) {
         if (c->warps < 1 || c->warps > 8 || c->rows < 1 || c->rows > 8) return false;
         return c->warps * c->rows <= 8;
     }
+    if (c->kind == 8)       // cluster-resident steps: cluster of up to `rows` CTAs
+        return !batched && c->cpt == 1 && c->ctas == 0 && (c->warps == 8 || c->warps == 16) &&
+               c->rows >= 2 && c->rows <= 16;
     // kinds 1 and 3 are not built (never the fastest at any measured size)
     if (c->kind < 2 || c->kind > 7 || c->kind == 3) return false;
     if (c->rows < 2 || c->rows > 6) return false;
@@ -261,6 +264,16 @@ int ensure_graph(vans_t h) {
 // nsteps steps; the parity lives in h->cur (single) or h->parity (batched)
 int run_steps(vans_t h, int nsteps) {
     int &par = h->batched ? h->parity : h->cur;
+    if (!h->batched && h->L.kind == 8 && nsteps > 0) {
+        // all the steps in one launch; the result lands where the step-by-step
+        // run would leave it
+        ++h->launches;
+        if (vans::launch_step_cluster(h->q, h->dom, h->st[par], h->st[par ^ (nsteps & 1)], nsteps,
+                                      h->L, h->stream) != cudaSuccess)
+            return VANS_ERR_CUDA;
+        par ^= nsteps & 1;
+        return VANS_OK;
+    }
     int left = nsteps;
     if (left >= 2) {
         if (par != 0) {
@@ -467,6 +480,10 @@ std::vector<Launch> candidates(int q, bool batched) {
                             {2, 4, 2, 5, 2}};
         c.insert(c.end(), std::begin(t), std::end(t));
     }
+    // cluster-resident multi-step shapes {1, warps, largest cluster, 8}; the
+    // autotuner skips those whose cluster cannot hold the domain
+    const Launch k8[] = {{1, 8, 16, 8}, {1, 16, 16, 8}, {1, 8, 8, 8}, {1, 16, 8, 8}};
+    c.insert(c.end(), std::begin(k8), std::end(k8));
     return c;
 }
 
@@ -671,6 +688,7 @@ int vans_set_launch(vans_t h, const vans_launch *cfg) {
     if (!h || !launch_ok(cfg, h->q, h->batched)) return VANS_ERR_ARG;
     const Launch L{cfg->cpt, cfg->warps, cfg->rows, cfg->kind, cfg->ctas};
     if (!h->batched && h->dom.nee && !vans::launch_has_plates(h->q, L)) return VANS_ERR_UNSUPPORTED;
+    if (L.kind == 8 && !vans::cluster_fits(h->q, h->dom, L.rows)) return VANS_ERR_UNSUPPORTED;
     if (h->batched) return set_batch_launch(h, L);
     h->L = L;
     drop_graph(h);
@@ -687,13 +705,21 @@ int vans_autotune(vans_t h, vans_launch *chosen) {
     float best_ms = 1e30f;
     const float *in = h->st[h->cur];
     float *outb = h->st[h->cur ^ 1];
-    const int reps = h->dom.cells > (1 << 22) ? 5 : 20;
+    const int reps = h->dom.cells > (1 << 22) ? 5 : 21;
     for (const Launch &L : cs) {
         if (h->dom.nee && !vans::launch_has_plates(h->q, L)) continue;   // no plate instance
-        const float ms = time_launches(
-            h, [&](cudaStream_t st) { return vans::launch_step(h->q, h->dom, in, outb, L, st); },
-            reps);
-        h->launches += 5 * reps;
+        if (L.kind == 8 && !vans::cluster_fits(h->q, h->dom, L.rows)) continue;
+        // kind 8 runs the reps steps in one launch (odd reps: the result
+        // lands in the spare buffer, as one step of the other kinds does)
+        const float ms =
+            L.kind == 8
+                ? time_launches(h, [&](cudaStream_t st) {
+                      return vans::launch_step_cluster(h->q, h->dom, in, outb, reps, L, st);
+                  }, 1)
+                : time_launches(h, [&](cudaStream_t st) {
+                      return vans::launch_step(h->q, h->dom, in, outb, L, st);
+                  }, reps);
+        h->launches += L.kind == 8 ? 5 : 5 * reps;
         if (ms < best_ms) {
             best_ms = ms;
             best = L;

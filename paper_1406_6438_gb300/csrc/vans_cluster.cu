@@ -1,0 +1,193 @@
+// vans_cluster.cu -- many steps in one launch for domains that fit in the
+// shared memory of one thread-block cluster (launch kind 8).
+//
+// A small domain (the 128x64 channel, the 80x80 Couette case) is a few
+// hundred KB of populations: one step is a few microseconds of launch
+// overhead around less than a microsecond of work.  Here one cluster of up to
+// 16 CTAs holds the whole state in its distributed shared memory for the
+// whole run: CTA k owns a band of consecutive rows (row = z * ny + y) and keeps
+// two copies of its band, the populations the step reads and the ones it
+// writes, each row with its halo columns -1 and nx.  A step is the same pull,
+// collision and store as every other kernel here (the functions of
+// vans_device.cuh, so the same arithmetic); a pull that crosses into another
+// band reads the owning CTA's shared memory through the cluster's
+// distributed shared memory window.  One cluster barrier per step separates
+// the writes of step t from the reads of step t + 1; because the two copies
+// alternate, the writes of step t + 1 (into the copy read at step t) also
+// come after every read of step t.  The band is loaded from the state buffer
+// `fin` at the start and written back to `fout` at the end (columns -1 .. nx
+// of every row and direction, the library's padded layout).
+#include <cooperative_groups.h>
+
+#include "vans_device.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace vans {
+
+namespace {
+
+constexpr int kClusterMax = 16;
+constexpr int kClusterSmemMax = 227 * 1024;
+
+// floats per row copy in shared memory: columns -1 .. nx, rounded up to 4
+__host__ __device__ inline int cluster_row_floats(int nx) { return (nx + 2 + 3) & ~3; }
+
+}  // namespace
+
+template <int Q, int NT>
+__global__ void __launch_bounds__(NT) k_step_cluster(const VDom d, const float *fin, float *fout,
+                                                     int nsteps, int band) {
+    using L = Lat<Q>;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int sp = cluster_row_floats(d.nx);
+    const long long copy = (long long)Q * band * sp;     // floats of one copy of a band
+    extern __shared__ __align__(16) float sm[];
+    const int r0 = rank * band;
+    const int nr = max(0, min(band, d.rows - r0));
+    const int nx = d.nx;
+
+    // the band's rows of the state buffer, columns -1 .. nx
+    for (long long t = threadIdx.x; t < (long long)Q * nr * (nx + 2); t += NT) {
+        const int c = (int)(t % (nx + 2));
+        const long long pr = t / (nx + 2);
+        const int rl = (int)(pr % nr), i = (int)(pr / nr);
+        sm[((long long)i * band + rl) * sp + c] =
+            fin[i * d.plane + (long long)(r0 + rl) * d.pitch + VANS_OFF - 1 + c];
+    }
+    cl.sync();
+
+    int b = 0;
+    for (int s = 0; s < nsteps; ++s) {
+        const float *cur = sm + b * copy;
+        float *nxt = sm + (b ^ 1) * copy;
+        for (int t = threadIdx.x; t < nr * nx; t += NT) {
+            const int rl = t / nx, x = t - rl * nx;
+            const int r = r0 + rl, y = r % d.ny, z = r / d.ny;
+            const Nb3 Y = nb3<true>(y, d.ny, d.wall_y);
+            Nb3 Z;
+            if (Q == 19) {
+                Z = nb3<true>(z, d.nz, d.wall_z);
+            } else {
+                Z.r[0] = Z.r[1] = Z.r[2] = 0;
+                Z.wall[0] = Z.wall[1] = Z.wall[2] = false;
+            }
+            // pull: the entry at x - e_i of row (y - e_y, z - e_z), or the
+            // opposite direction of this cell past a wall; that row lives in
+            // the band of CTA row / band
+            float h[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const int ey = L::ey(i), ez = L::ez(i);
+                const bool bb = Y.wall[1 - ey] || Z.wall[1 - ez];
+                const int sr = bb ? r : Z.r[1 - ez] * d.ny + Y.r[1 - ey];
+                const int owner = sr / band;
+                const float *base = (owner == rank) ? cur : cl.map_shared_rank(cur, owner);
+                const int plane = bb ? L::opp(i) : i;
+                const int col = bb ? x : x - L::ex(i);
+                h[i] = base[((long long)plane * band + (sr - owner * band)) * sp + col + 1];
+            }
+            // porosity of the cell and of its neighbours (padded rows, L1-resident)
+            const float e0 = __ldg(d.eps + row_offset(d, y, z) + x);
+            float et[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const bool wall = Y.wall[1 + L::ey(i)] || Z.wall[1 + L::ez(i)];
+                et[i] = (i == 0 || wall)
+                            ? e0
+                            : __ldg(d.eps + row_offset(d, Y.r[1 + L::ey(i)], Z.r[1 + L::ez(i)]) + x +
+                                    L::ex(i));
+            }
+            apply_moving_wall<Q>(d, Y.wall[2], Z, e0, h);
+            float o[Q];
+            collide<Q>(d, h, e0, et, o);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                float *row = nxt + ((long long)i * band + rl) * sp + 1;   // column 0
+                row[x] = o[i];
+                if (x == 0 && L::ex(i) < 0) row[nx] = o[i];       // halo copies of the wrap
+                if (x == nx - 1 && L::ex(i) > 0) row[-1] = o[i];
+            }
+        }
+        cl.sync();
+        b ^= 1;
+    }
+
+    const float *res = sm + b * copy;
+    for (long long t = threadIdx.x; t < (long long)Q * nr * (nx + 2); t += NT) {
+        const int c = (int)(t % (nx + 2));
+        const long long pr = t / (nx + 2);
+        const int rl = (int)(pr % nr), i = (int)(pr / nr);
+        fout[i * d.plane + (long long)(r0 + rl) * d.pitch + VANS_OFF - 1 + c] =
+            res[((long long)i * band + rl) * sp + c];
+    }
+}
+
+// Rows per CTA and CTAs of the cluster for a cluster of at most cmax CTAs.
+static void cluster_shape(const VDom &d, int cmax, int &band, int &ctas) {
+    band = (d.rows + cmax - 1) / cmax;
+    ctas = (d.rows + band - 1) / band;
+}
+
+size_t cluster_smem_bytes(int q, const VDom &d, int cmax) {
+    int band = 0, ctas = 0;
+    cluster_shape(d, cmax, band, ctas);
+    return 2 * (size_t)q * band * cluster_row_floats(d.nx) * sizeof(float);
+}
+
+bool cluster_fits(int q, const VDom &d, int cmax) {
+    if (d.nee || cmax < 1 || cmax > kClusterMax) return false;
+    return cluster_smem_bytes(q, d, cmax) <= (size_t)kClusterSmemMax;
+}
+
+template <int Q, int NT>
+static cudaError_t launch_cluster_t(const VDom &d, const float *fin, float *fout, int nsteps,
+                                    int cmax, cudaStream_t stream) {
+    int band = 0, ctas = 0;
+    cluster_shape(d, cmax, band, ctas);
+    const size_t smem = cluster_smem_bytes(Q, d, cmax);
+    auto kern = k_step_cluster<Q, NT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (ctas > 8) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ctas, 1, 1);
+    cfg.blockDim = dim3(NT, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = ctas;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    e = cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg);
+    if (e != cudaSuccess) return e;
+    if (nclusters < 1) return cudaErrorInvalidConfiguration;
+    e = cudaLaunchKernelEx(&cfg, kern, d, fin, fout, nsteps, band);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+// kind 8: `warps` warps per CTA (8 or 16), `rows` = the largest cluster (2..16)
+cudaError_t launch_step_cluster(int q, const VDom &d, const float *fin, float *fout, int nsteps,
+                                Launch L, cudaStream_t stream) {
+    if (nsteps < 1) return cudaErrorInvalidValue;
+    if (!cluster_fits(q, d, L.rows)) return cudaErrorInvalidValue;
+    if (q == 9) {
+        if (L.warps == 8) return launch_cluster_t<9, 256>(d, fin, fout, nsteps, L.rows, stream);
+        if (L.warps == 16) return launch_cluster_t<9, 512>(d, fin, fout, nsteps, L.rows, stream);
+    } else if (q == 19) {
+        if (L.warps == 8) return launch_cluster_t<19, 256>(d, fin, fout, nsteps, L.rows, stream);
+        if (L.warps == 16) return launch_cluster_t<19, 512>(d, fin, fout, nsteps, L.rows, stream);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace vans

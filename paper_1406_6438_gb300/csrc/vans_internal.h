@@ -46,8 +46,10 @@ struct Tile {
 };
 
 // kind 0: register-load kernel k_step (cpt cells per lane, warps x rows per block)
-// kinds 2, 4-7: bulk-copy pipelines (32*warps compute threads, cpt cells per
+// kinds 2-7: bulk-copy pipelines (32*warps compute threads, cpt cells per
 //         thread per tile, rows = pipeline stages)
+// kind 8: cluster-resident multi-step kernel (32*warps threads per CTA, rows =
+//         the largest cluster)
 // ctas: at most that many CTAs per SM for the pipelined kinds (0: as many as fit)
 struct Launch {
     int cpt, warps, rows, kind;
@@ -72,6 +74,12 @@ cudaError_t launch_step_monitor(int q, const VDom &d, const float *fin, float *f
                                 float *u, float *stats, cudaStream_t stream);
 cudaError_t launch_step_tma(int q, const VDom &d, const float *fin, float *fout, Launch L,
                             cudaStream_t stream);
+// kind 8: nsteps steps in one launch of one thread-block cluster that holds the
+// whole state in its shared memory; reads fin, writes fout (which may be fin)
+cudaError_t launch_step_cluster(int q, const VDom &d, const float *fin, float *fout, int nsteps,
+                                Launch L, cudaStream_t stream);
+// whether a cluster of at most cmax CTAs holds the domain (never plates on nodes)
+bool cluster_fits(int q, const VDom &d, int cmax);
 // the reverse step with a bulk-copy pipeline (adjoint launch kind 1)
 cudaError_t launch_adjoint_tma(int q, const VDom &d, const float *state, const float *lam_in,
                                float *lam_out, float *grad, int fp64, Launch L, cudaStream_t s);

@@ -236,6 +236,7 @@ static cudaError_t launch_step_t(const VDom &d, const float *fin, float *fout, L
 cudaError_t launch_step(int q, const VDom &d, const float *fin, float *fout, Launch L,
                         cudaStream_t stream) {
     if (L.kind >= 1 && L.kind <= 7) return launch_step_tma(q, d, fin, fout, L, stream);
+    if (L.kind == 8) return launch_step_cluster(q, d, fin, fout, 1, L, stream);
     if (L.kind != 0) return cudaErrorInvalidValue;
     if (q == 9) {
         switch (L.cpt) {
