@@ -283,9 +283,10 @@ def bench_d3q19(torch, V, W, args=None):
 
 
 def bench_channel(torch, V, W, args=None):
-    """The 128 x 64 porous Poiseuille channel (the parity workload): 5000
-    graph-replayed steps.  Its 0.6 MB buffers stay in L2 and a step is a few
-    microseconds, so the figure is MLUPS only, not an HBM fraction."""
+    """The 128 x 64 porous Poiseuille channel (the parity workload): its 5000
+    steps in the autotuned launch (kind 8 when one thread-block cluster holds
+    the state: all of them in one launch).  The 0.6 MB state never leaves the
+    chip, so the figure is MLUPS only, not an HBM fraction."""
     p, eps, n = W.channel_128x64()
     s = V.Solver(p)
     s.set_eps(torch.from_numpy(eps).cuda().view(-1))
@@ -297,7 +298,8 @@ def bench_channel(torch, V, W, args=None):
     out = {"workload": "D2Q9 porous Poiseuille channel 128x64, eps 0.6, Da 1e-3, tau 0.8",
            "steps": n, "value": cells * n / t / 1e6, "unit": "MLUPS", "us_per_step": t / n * 1e6,
            "launch": vars(L), "launches": s.launch_count - c0,
-           "note": "L2-resident and launch-bound: no HBM fraction"}
+           "note": ("state resident on chip (kind 8: a cluster's shared memory; otherwise L2): "
+                    "no HBM fraction")}
     s.close()
     return out
 

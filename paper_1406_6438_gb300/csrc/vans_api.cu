@@ -688,7 +688,7 @@ int vans_set_launch(vans_t h, const vans_launch *cfg) {
     if (!h || !launch_ok(cfg, h->q, h->batched)) return VANS_ERR_ARG;
     const Launch L{cfg->cpt, cfg->warps, cfg->rows, cfg->kind, cfg->ctas};
     if (!h->batched && h->dom.nee && !vans::launch_has_plates(h->q, L)) return VANS_ERR_UNSUPPORTED;
-    if (L.kind == 8 && !vans::cluster_fits(h->q, h->dom, L.rows)) return VANS_ERR_UNSUPPORTED;
+    if (L.kind == 8 && !vans::cluster_fits(h->q, h->dom, L.rows, L.warps)) return VANS_ERR_UNSUPPORTED;
     if (h->batched) return set_batch_launch(h, L);
     h->L = L;
     drop_graph(h);
@@ -708,7 +708,7 @@ int vans_autotune(vans_t h, vans_launch *chosen) {
     const int reps = h->dom.cells > (1 << 22) ? 5 : 21;
     for (const Launch &L : cs) {
         if (h->dom.nee && !vans::launch_has_plates(h->q, L)) continue;   // no plate instance
-        if (L.kind == 8 && !vans::cluster_fits(h->q, h->dom, L.rows)) continue;
+        if (L.kind == 8 && !vans::cluster_fits(h->q, h->dom, L.rows, L.warps)) continue;
         // kind 8 runs the reps steps in one launch (odd reps: the result
         // lands in the spare buffer, as one step of the other kinds does)
         const float ms =

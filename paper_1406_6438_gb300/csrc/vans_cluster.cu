@@ -33,12 +33,39 @@ constexpr int kClusterSmemMax = 227 * 1024;
 // floats per row copy in shared memory: columns -1 .. nx, rounded up to 4
 __host__ __device__ inline int cluster_row_floats(int nx) { return (nx + 2 + 3) & ~3; }
 
+// cells per thread at most: D2Q9 2, D3Q19 1 (its 19 addresses and porosities
+// per cell stay in registers for the whole launch)
+template <int Q> struct CellsMax { static constexpr int N = (Q == 9) ? 2 : 1; };
+
+// Address, in the cluster's shared-memory window, of `local` (a shared-memory
+// address of this CTA) in the shared memory of CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t cluster_addr(const float *local, int rank) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(local);
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ float ld_cluster(uint32_t addr) {
+    float v;
+    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr));
+    return v;
+}
+
 }  // namespace
 
+// Every thread keeps at most CellsMax<Q>::N cells of its CTA's band for the
+// whole launch.  What a cell's update needs besides the populations does not
+// change from step to step, so it is formed once, before the first step: the
+// address (in the cluster's shared-memory window, so in the shared memory of
+// the CTA that owns the row) of each of the Q entries its pull reads, and its
+// own and its neighbours' porosities.  A step is then Q loads, the collision
+// and Q stores per cell.
 template <int Q, int NT>
 __global__ void __launch_bounds__(NT) k_step_cluster(const VDom d, const float *fin, float *fout,
                                                      int nsteps, int band) {
     using L = Lat<Q>;
+    constexpr int kCellsMax = CellsMax<Q>::N;
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     const int sp = cluster_row_floats(d.nx);
@@ -56,58 +83,78 @@ __global__ void __launch_bounds__(NT) k_step_cluster(const VDom d, const float *
         sm[((long long)i * band + rl) * sp + c] =
             fin[i * d.plane + (long long)(r0 + rl) * d.pitch + VANS_OFF - 1 + c];
     }
+
+    // per cell, fixed for the launch: pull addresses (copy 0), porosities,
+    // the row offset of its stores, and whether it sits under a moving wall
+    uint32_t src[kCellsMax][Q];
+    float e0[kCellsMax], et[kCellsMax][Q];
+    int dst[kCellsMax], xs[kCellsMax];
+    bool top[kCellsMax], live[kCellsMax];
+    Nb3 Zs[kCellsMax];
+#pragma unroll
+    for (int k = 0; k < kCellsMax; ++k) {
+        const int t = threadIdx.x + k * NT;
+        live[k] = t < nr * nx;
+        const int tt = live[k] ? t : 0;
+        const int rl = tt / nx, x = tt - rl * nx;
+        const int r = r0 + rl, y = r % d.ny, z = r / d.ny;
+        const Nb3 Y = nb3<true>(y, d.ny, d.wall_y);
+        Nb3 Z;
+        if (Q == 19) {
+            Z = nb3<true>(z, d.nz, d.wall_z);
+        } else {
+            Z.r[0] = Z.r[1] = Z.r[2] = 0;
+            Z.wall[0] = Z.wall[1] = Z.wall[2] = false;
+        }
+        Zs[k] = Z;
+        top[k] = Y.wall[2];
+        xs[k] = x;
+        dst[k] = rl * sp + 1 + x;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            // the entry at x - e_i of row (y - e_y, z - e_z), or the opposite
+            // direction of this cell past a wall; that row lives in the band
+            // of CTA row / band
+            const int ey = L::ey(i), ez = L::ez(i);
+            const bool bb = Y.wall[1 - ey] || Z.wall[1 - ez];
+            const int sr = bb ? r : Z.r[1 - ez] * d.ny + Y.r[1 - ey];
+            const int owner = sr / band;
+            const int plane = bb ? L::opp(i) : i;
+            const int col = bb ? x : x - L::ex(i);
+            src[k][i] = cluster_addr(sm + ((long long)plane * band + (sr - owner * band)) * sp +
+                                         col + 1, owner);
+        }
+        e0[k] = live[k] ? __ldg(d.eps + row_offset(d, y, z) + x) : 1.f;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const bool wall = Y.wall[1 + L::ey(i)] || Z.wall[1 + L::ez(i)];
+            et[k][i] = (i == 0 || wall || !live[k])
+                           ? e0[k]
+                           : __ldg(d.eps + row_offset(d, Y.r[1 + L::ey(i)], Z.r[1 + L::ez(i)]) + x +
+                                   L::ex(i));
+        }
+    }
     cl.sync();
 
     int b = 0;
     for (int s = 0; s < nsteps; ++s) {
-        const float *cur = sm + b * copy;
+        const uint32_t cur = (uint32_t)(b * copy * sizeof(float));   // the copy read this step
         float *nxt = sm + (b ^ 1) * copy;
-        for (int t = threadIdx.x; t < nr * nx; t += NT) {
-            const int rl = t / nx, x = t - rl * nx;
-            const int r = r0 + rl, y = r % d.ny, z = r / d.ny;
-            const Nb3 Y = nb3<true>(y, d.ny, d.wall_y);
-            Nb3 Z;
-            if (Q == 19) {
-                Z = nb3<true>(z, d.nz, d.wall_z);
-            } else {
-                Z.r[0] = Z.r[1] = Z.r[2] = 0;
-                Z.wall[0] = Z.wall[1] = Z.wall[2] = false;
-            }
-            // pull: the entry at x - e_i of row (y - e_y, z - e_z), or the
-            // opposite direction of this cell past a wall; that row lives in
-            // the band of CTA row / band
+#pragma unroll
+        for (int k = 0; k < kCellsMax; ++k) {
+            if (!live[k]) continue;
             float h[Q];
 #pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const int ey = L::ey(i), ez = L::ez(i);
-                const bool bb = Y.wall[1 - ey] || Z.wall[1 - ez];
-                const int sr = bb ? r : Z.r[1 - ez] * d.ny + Y.r[1 - ey];
-                const int owner = sr / band;
-                const float *base = (owner == rank) ? cur : cl.map_shared_rank(cur, owner);
-                const int plane = bb ? L::opp(i) : i;
-                const int col = bb ? x : x - L::ex(i);
-                h[i] = base[((long long)plane * band + (sr - owner * band)) * sp + col + 1];
-            }
-            // porosity of the cell and of its neighbours (padded rows, L1-resident)
-            const float e0 = __ldg(d.eps + row_offset(d, y, z) + x);
-            float et[Q];
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const bool wall = Y.wall[1 + L::ey(i)] || Z.wall[1 + L::ez(i)];
-                et[i] = (i == 0 || wall)
-                            ? e0
-                            : __ldg(d.eps + row_offset(d, Y.r[1 + L::ey(i)], Z.r[1 + L::ez(i)]) + x +
-                                    L::ex(i));
-            }
-            apply_moving_wall<Q>(d, Y.wall[2], Z, e0, h);
+            for (int i = 0; i < Q; ++i) h[i] = ld_cluster(src[k][i] + cur);
+            apply_moving_wall<Q>(d, top[k], Zs[k], e0[k], h);
             float o[Q];
-            collide<Q>(d, h, e0, et, o);
+            collide<Q>(d, h, e0[k], et[k], o);
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
-                float *row = nxt + ((long long)i * band + rl) * sp + 1;   // column 0
-                row[x] = o[i];
-                if (x == 0 && L::ex(i) < 0) row[nx] = o[i];       // halo copies of the wrap
-                if (x == nx - 1 && L::ex(i) > 0) row[-1] = o[i];
+                float *row = nxt + (long long)i * band * sp + dst[k];   // this cell's column
+                row[0] = o[i];
+                if (xs[k] == 0 && L::ex(i) < 0) row[nx] = o[i];         // halo copies of the wrap
+                if (xs[k] == nx - 1 && L::ex(i) > 0) row[-nx] = o[i];
             }
         }
         cl.sync();
@@ -136,8 +183,12 @@ size_t cluster_smem_bytes(int q, const VDom &d, int cmax) {
     return 2 * (size_t)q * band * cluster_row_floats(d.nx) * sizeof(float);
 }
 
-bool cluster_fits(int q, const VDom &d, int cmax) {
+bool cluster_fits(int q, const VDom &d, int cmax, int warps) {
     if (d.nee || cmax < 1 || cmax > kClusterMax) return false;
+    int band = 0, ctas = 0;
+    cluster_shape(d, cmax, band, ctas);
+    const int cells_max = (q == 9) ? CellsMax<9>::N : CellsMax<19>::N;
+    if ((long long)band * d.nx > (long long)cells_max * 32 * warps) return false;
     return cluster_smem_bytes(q, d, cmax) <= (size_t)kClusterSmemMax;
 }
 
@@ -179,7 +230,7 @@ static cudaError_t launch_cluster_t(const VDom &d, const float *fin, float *fout
 cudaError_t launch_step_cluster(int q, const VDom &d, const float *fin, float *fout, int nsteps,
                                 Launch L, cudaStream_t stream) {
     if (nsteps < 1) return cudaErrorInvalidValue;
-    if (!cluster_fits(q, d, L.rows)) return cudaErrorInvalidValue;
+    if (!cluster_fits(q, d, L.rows, L.warps)) return cudaErrorInvalidValue;
     if (q == 9) {
         if (L.warps == 8) return launch_cluster_t<9, 256>(d, fin, fout, nsteps, L.rows, stream);
         if (L.warps == 16) return launch_cluster_t<9, 512>(d, fin, fout, nsteps, L.rows, stream);

@@ -78,8 +78,9 @@ cudaError_t launch_step_tma(int q, const VDom &d, const float *fin, float *fout,
 // whole state in its shared memory; reads fin, writes fout (which may be fin)
 cudaError_t launch_step_cluster(int q, const VDom &d, const float *fin, float *fout, int nsteps,
                                 Launch L, cudaStream_t stream);
-// whether a cluster of at most cmax CTAs holds the domain (never plates on nodes)
-bool cluster_fits(int q, const VDom &d, int cmax);
+// whether a cluster of at most cmax CTAs of `warps` warps holds the domain
+// (never plates on nodes)
+bool cluster_fits(int q, const VDom &d, int cmax, int warps);
 // the reverse step with a bulk-copy pipeline (adjoint launch kind 1)
 cudaError_t launch_adjoint_tma(int q, const VDom &d, const float *state, const float *lam_in,
                                float *lam_out, float *grad, int fp64, Launch L, cudaStream_t s);
