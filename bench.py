@@ -290,7 +290,14 @@ def bench_channel(torch, V, W, args=None):
     p, eps, n = W.channel_128x64()
     s = V.Solver(p)
     s.set_eps(torch.from_numpy(eps).cuda().view(-1))
-    L = s.autotune()
+    fl = fixed_launch(args.launch) if args is not None else None
+    if fl:
+        s.launch = V.Launch(*fl)
+        L = s.launch
+    else:
+        L = s.autotune()
+    if args is not None and args.only == "channel":
+        n = args.steps
     s.step(64)
     c0 = s.launch_count
     t = time_region(torch, s.stream, lambda: s.step(n))
@@ -428,7 +435,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--launch", default=None,
                     help="fixed launch shape cpt,warps,rows[,kind] instead of the autotuner")
-    ap.add_argument("--only", default=None, choices=["d3q19", "batched", "adjoint"],
+    ap.add_argument("--only", default=None, choices=["d3q19", "batched", "adjoint", "channel"],
                     help="run one side benchmark alone (profiling captures) and print its JSON")
     ap.add_argument("--dims", default=None, help="nx,ny,nz of the D3Q19 duct for --only d3q19")
     ap.add_argument("--domains", type=int, default=0, help="domains for --only batched")
@@ -440,7 +447,8 @@ def main():
         import torch
         import paper_1406_6438_gb300 as V
         from paper_1406_6438_gb300 import workloads as W
-        fn = {"d3q19": bench_d3q19, "batched": bench_batched, "adjoint": bench_adjoint}[args.only]
+        fn = {"d3q19": bench_d3q19, "batched": bench_batched, "adjoint": bench_adjoint,
+              "channel": bench_channel}[args.only]
         print(json.dumps({args.only: fn(torch, V, W, args)}), flush=True)
         return 0
 

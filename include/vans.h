@@ -318,10 +318,11 @@ long long vans_batch_cells(vans_t h);
  * buffers, the padded copy of eps (dense nx*ny*nz floats, 0 < eps <= 1; not
  * range-checked here), is a 16 MiB array that the library holds in device
  * memory on every GPU where it is loaded, until the process exits.
- * Limit: ny*nz rows times the padded row length (nx rounded up to 128, plus 9,
- * rounded up to 32 floats) must not exceed 4 Mi floats, e.g. a D2Q9 domain of
- * 2048 x 2016 cells, or a D3Q19 cube of up to 128^3 (from 129 cells on the
- * padded row jumps to 288 floats); larger domains get VANS_ERR_ARG.
+ * Limit: ny*nz rows times the padded row length (nx rounded up to 128, plus 9
+ * for D2Q9 or 33 for D3Q19, rounded up to 32 floats) must not exceed 4 Mi
+ * floats, e.g. a D2Q9 domain of 2048 x 2016
+ * cells, or a D3Q19 cube of up to 128^3 (from 129 cells on the padded row
+ * jumps to 320 floats); larger domains get VANS_ERR_ARG.
  * Parameter errors as in vans_create.  The first call on a device looks up the
  * array's device address; make that first call before any stream capture.
  * All calls share the array, so calls whose GPU work overlaps (on different

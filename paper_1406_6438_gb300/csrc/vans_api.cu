@@ -34,12 +34,12 @@ long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
 using vans::pitch_for;
 
 long long state_floats_of(int q, int nx, int ny, int nz) {
-    const long long plane = (long long)ny * nz * pitch_for(nx);
+    const long long plane = (long long)ny * nz * pitch_for(q, nx);
     return round_up((long long)q * plane, 64);
 }
 
-long long eps_floats_of(int nx, int ny, int nz) {
-    return round_up((long long)ny * nz * pitch_for(nx), 64);
+long long eps_floats_of(int q, int nx, int ny, int nz) {
+    return round_up((long long)ny * nz * pitch_for(q, nx), 64);
 }
 
 constexpr long long kFlagFloats = 64;   // 256 bytes of status words
@@ -108,8 +108,8 @@ bool launch_ok(const vans_launch *c, int q, bool batched) {
 
 namespace vans {
 
-int pitch_for(int nx) {
-    return (int)((VANS_OFF + ((long long)nx + 127) / 128 * 128 + 1 + 31) / 32 * 32);
+int pitch_for(int q, int nx) {
+    return (int)((col0_for(q) + ((long long)nx + 127) / 128 * 128 + 1 + 31) / 32 * 32);
 }
 
 // Host-side constants of the drag law: alpha = ca * a(eps), beta = cb * b(eps).
@@ -120,7 +120,9 @@ void fill_dom(const vans_params *p, VDom &d) {
     d.ny = p->ny;
     d.nz = p->nz;
     d.rows = p->ny * p->nz;
-    d.pitch = pitch_for(p->nx);
+    d.pitch = pitch_for(p->q, p->nx);
+    d.off = col0_for(p->q);
+    d.xwrap = 1;
     d.plane = (long long)d.rows * d.pitch;
     d.wall_y = (p->wall_mask >> 1) & 1;
     d.wall_z = (p->wall_mask >> 2) & 1;
@@ -337,7 +339,9 @@ int reset_to_rest(vans_t h) {
     }
     h->cur = 0;
     h->eps_set = true;
+    if (h->slab) drop_graph(h);
     h->slab = false;
+    h->dom.xwrap = 1;
     return VANS_OK;
 }
 
@@ -357,8 +361,12 @@ void build_tiles(vans_t h, const Launch &L, std::vector<Tile> &out) {
         return;
     }
     if (L.kind != 0) {
-        // strips of up to kStripRows rows per column block, largest first so the
-        // last wave of CTAs holds the short ones
+        // strips of up to kStripRows rows per column block.  The column blocks
+        // of one band of rows stay next to each other in the table, so their
+        // CTAs run at the same time and the 128-byte line two neighbouring
+        // blocks both stage (the halo column of each) comes from DRAM once;
+        // bands go largest first (rows x the domain's width), so the last wave
+        // of CTAs holds the short ones
         for (int d = 0; d < h->n; ++d) {
             const VDom &D = h->doms[d];
             const int per_y = (D.ny + kStripRows - 1) / kStripRows;
@@ -369,8 +377,8 @@ void build_tiles(vans_t h, const Launch &L, std::vector<Tile> &out) {
             }
         }
         std::stable_sort(out.begin(), out.end(), [&](const Tile &a, const Tile &b) {
-            const long long wa = (long long)(a.pad - a.row) * std::min(bx, h->doms[a.dom].nx - a.x0);
-            const long long wb = (long long)(b.pad - b.row) * std::min(bx, h->doms[b.dom].nx - b.x0);
+            const long long wa = (long long)(a.pad - a.row) * h->doms[a.dom].nx;
+            const long long wb = (long long)(b.pad - b.row) * h->doms[b.dom].nx;
             return wa > wb;
         });
         return;
@@ -477,7 +485,7 @@ std::vector<Launch> candidates(int q, bool batched) {
                             {2, 4, 3, 5}, {2, 4, 4, 5}, {2, 2, 3, 5}, {1, 4, 3, 6},
                             {1, 8, 3, 6}, {2, 4, 3, 7}, {2, 2, 3, 7}, {2, 4, 2, 7},
                             {2, 4, 2, 7, 2}, {2, 4, 2, 7, 1}, {2, 4, 3, 7, 1}, {2, 4, 3, 7, 2},
-                            {2, 4, 2, 5, 2}};
+                            {2, 4, 2, 5, 2}, {2, 2, 2, 7}, {2, 2, 4, 7}};
         c.insert(c.end(), std::begin(t), std::end(t));
     }
     // cluster-resident multi-step shapes {1, warps, largest cluster, 8}; the
@@ -500,7 +508,7 @@ long long vans_state_floats(const vans_params *p) {
 size_t vans_workspace_bytes(const vans_params *p) {
     if (validate(p, false) != VANS_OK) return 0;
     const long long f = 2 * state_floats_of(p->q, p->nx, p->ny, p->nz) +
-                        eps_floats_of(p->nx, p->ny, p->nz) + kFlagFloats;
+                        eps_floats_of(p->q, p->nx, p->ny, p->nz) + kFlagFloats;
     return (size_t)f * sizeof(float);
 }
 
@@ -522,7 +530,7 @@ int vans_create(const vans_params *p, void *workspace, size_t workspace_bytes, v
     h->st[0] = w;
     h->st[1] = w + h->sfloats;
     h->eps_pad = w + 2 * h->sfloats;
-    h->flag = (int *)(h->eps_pad + eps_floats_of(p->nx, p->ny, p->nz));
+    h->flag = (int *)(h->eps_pad + eps_floats_of(p->q, p->nx, p->ny, p->nz));
     h->dom.eps = h->eps_pad;
     h->dom.status = h->flag + 1;
     h->L = (p->q == 9) ? Launch{4, 4, 1, 0} : Launch{2, 4, 1, 0};
@@ -914,6 +922,8 @@ int vans_set_eps_slab(vans_t h, const float *eps_dev, const float *eps_left,
         cudaSuccess)
         return VANS_ERR_CUDA;
     h->slab = true;
+    h->dom.xwrap = 0;            // the halo columns are the neighbours', not the row's own ends
+    drop_graph(h);
     return VANS_OK;
 }
 
@@ -955,7 +965,7 @@ size_t vans_batch_workspace_bytes(const vans_params *p, int n) {
                       round_up(batch_tile_cap(p, n) * (long long)sizeof(Tile), 256);
     for (int d = 0; d < n; ++d) {
         if (validate(&p[d], true) != VANS_OK) return 0;
-        bytes += (2 * state_floats_of(9, p[d].nx, p[d].ny, 1) + eps_floats_of(p[d].nx, p[d].ny, 1)) *
+        bytes += (2 * state_floats_of(9, p[d].nx, p[d].ny, 1) + eps_floats_of(9, p[d].nx, p[d].ny, 1)) *
                  (long long)sizeof(float);
     }
     bytes += kFlagFloats * sizeof(float);
@@ -997,7 +1007,7 @@ int vans_batch_create(const vans_params *p, int n, void *workspace, size_t works
         D.eps = (float *)w + 2 * sf;
         D.dense_off = dense;
         dense += D.cells;
-        w += (2 * sf + eps_floats_of(p[d].nx, p[d].ny, 1)) * sizeof(float);
+        w += (2 * sf + eps_floats_of(9, p[d].nx, p[d].ny, 1)) * sizeof(float);
     }
     h->flag = (int *)w;
     for (VDom &D : h->doms) D.status = h->flag + 1;

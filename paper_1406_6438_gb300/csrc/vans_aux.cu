@@ -128,6 +128,21 @@ __global__ void k_export(const VDom d, const float *__restrict__ st, float *__re
     }
 }
 
+// Write v into the entry the pull of cell (x,y,z) reads for direction i; a halo
+// entry (column -1 or nx) also goes to its mirror at the row's other end
+// (column nx-1 or 0), so that the two copies the step kernels leave agree after
+// any write: kernels that stage rows without their halo columns read the mirror.
+template <int Q>
+__device__ __forceinline__ void store_pulled(const VDom &d, float *__restrict__ st, int i, int x,
+                                             int y, int z, const Nb3 &Y, const Nb3 &Z, float v) {
+    using L = Lat<Q>;
+    const long long k = pull_index<Q>(d, i, x, y, z, Y, Z);
+    st[k] = v;
+    const bool bb = Y.wall[1 - L::ey(i)] || Z.wall[1 - L::ez(i)];
+    if (!bb && L::ex(i) > 0 && x == 0) st[k + d.nx] = v;            // column -1 -> nx-1
+    if (!bb && L::ex(i) < 0 && x == d.nx - 1) st[k - d.nx] = v;     // column nx -> 0
+}
+
 // inverse of k_export: writes every live entry of the state
 template <int Q>
 __global__ void k_import(const VDom d, const float *__restrict__ f, float *__restrict__ st) {
@@ -144,7 +159,7 @@ __global__ void k_import(const VDom d, const float *__restrict__ f, float *__res
         for (int i = 0; i < Q; ++i) {
             float v = f[i * d.cells + n] - L::w(i) * e0;
             if (top && L::ey(i) < 0 && !Z.wall[1 - L::ez(i)]) v -= wall_gain<Q>(d, i, e0);
-            st[pull_index<Q>(d, i, x, y, z, Y, Z)] = v;
+            store_pulled<Q>(d, st, i, x, y, z, Y, Z, v);
         }
     }
 }
@@ -194,7 +209,7 @@ __global__ void k_rebase_eps(const VDom d, const float *__restrict__ eps_new, fl
             float v = st[k] + L::w(i) * (e_old - e_new);
             if (top && L::ey(i) < 0 && !Z.wall[1 - L::ez(i)])
                 v += wall_gain<Q>(d, i, e_old) - wall_gain<Q>(d, i, e_new);
-            st[k] = v;
+            store_pulled<Q>(d, st, i, x, y, z, Y, Z, v);
         }
     }
 }
@@ -207,7 +222,7 @@ __global__ void k_pad_eps(const VDom d, const float *__restrict__ eps, float *__
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
         const long long r = t / d.pitch;
-        const int c = (int)(t % d.pitch) - VANS_OFF;
+        const int c = (int)(t % d.pitch) - d.off;
         float v = 1.0f;
         if (c >= 0 && c < d.nx) {
             v = eps[r * d.nx + c];
@@ -511,7 +526,7 @@ __global__ void k_halo_pack(const VDom d, const float *__restrict__ st, float *_
          t += (long long)gridDim.x * blockDim.x) {
         const int k = (int)(t / d.rows);
         const long long r = t - (long long)k * d.rows;
-        const long long ro = r * d.pitch + VANS_OFF;
+        const long long ro = r * d.pitch + d.off;
         int ip = 0, im = 0;
 #pragma unroll
         for (int j = 0; j < NX; ++j)
@@ -530,7 +545,7 @@ __global__ void k_halo_unpack(const VDom d, float *__restrict__ st, const float 
          t += (long long)gridDim.x * blockDim.x) {
         const int k = (int)(t / d.rows);
         const long long r = t - (long long)k * d.rows;
-        const long long ro = r * d.pitch + VANS_OFF;
+        const long long ro = r * d.pitch + d.off;
         int ip = 0, im = 0;
 #pragma unroll
         for (int j = 0; j < NX; ++j)
@@ -550,8 +565,8 @@ __global__ void k_eps_halo(const VDom d, const float *__restrict__ left,
         const float a = left[r], b = right[r];
         if (!(a > 0.0f && a <= 1.0f) || !(b > 0.0f && b <= 1.0f)) atomicOr(flag, 1);
         if (pad) {
-            pad[r * d.pitch + VANS_OFF - 1] = a;
-            pad[r * d.pitch + VANS_OFF + d.nx] = b;
+            pad[r * d.pitch + d.off - 1] = a;
+            pad[r * d.pitch + d.off + d.nx] = b;
         }
     }
 }

@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(NT) k_step_cluster(const VDom d, const float *
         const long long pr = t / (nx + 2);
         const int rl = (int)(pr % nr), i = (int)(pr / nr);
         sm[((long long)i * band + rl) * sp + c] =
-            fin[i * d.plane + (long long)(r0 + rl) * d.pitch + VANS_OFF - 1 + c];
+            fin[i * d.plane + (long long)(r0 + rl) * d.pitch + d.off - 1 + c];
     }
 
     // per cell, fixed for the launch: pull addresses (copy 0), porosities,
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(NT) k_step_cluster(const VDom d, const float *
         const int c = (int)(t % (nx + 2));
         const long long pr = t / (nx + 2);
         const int rl = (int)(pr % nr), i = (int)(pr / nr);
-        fout[i * d.plane + (long long)(r0 + rl) * d.pitch + VANS_OFF - 1 + c] =
+        fout[i * d.plane + (long long)(r0 + rl) * d.pitch + d.off - 1 + c] =
             res[((long long)i * band + rl) * sp + c];
     }
 }

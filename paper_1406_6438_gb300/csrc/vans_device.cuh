@@ -3,7 +3,7 @@
 // State layout.  One state buffer holds Q planes, one per direction i; a plane
 // holds rows = ny*nz padded rows of `pitch` floats (pitch is a multiple of 32
 // floats, so every row starts on a 128-byte boundary).  Column c of a row lives
-// at row + VANS_OFF + c for c in [-1, nx]: columns -1 and nx are halo copies
+// at row + d.off + c for c in [-1, nx]: columns -1 and nx are halo copies
 // that make the periodic x wrap free for the pull.  What a plane stores for cell
 // x is the post-collision population of direction i of the previous step, as a
 // deviation from w_i * eps~(x + e_i), the porosity of the cell it streams to
@@ -254,7 +254,7 @@ __device__ __forceinline__ Nb3 nb3(int c, int n, int walls) {
 }
 
 __device__ __forceinline__ long long row_offset(const VDom &d, int y, int z) {
-    return ((long long)z * d.ny + y) * d.pitch + VANS_OFF;
+    return ((long long)z * d.ny + y) * d.pitch + d.off;
 }
 
 // Moving upper wall: a population pulled through the upper y wall (direction

@@ -7,7 +7,9 @@
 
 #include "vans.h"
 
-#define VANS_OFF 8  // column 0 of a padded row sits 8 floats (one 32-byte sector) into the row
+// Column 0 of a padded row sits VDom::off floats into the row: 8 (one 32-byte
+// sector) for D2Q9, 32 (one 128-byte line) for D3Q19, whose rows of a few
+// hundred cells are staged whole, cells only, so that they cover whole lines.
 
 namespace vans {
 
@@ -18,6 +20,9 @@ struct VDom {
     int q, nx, ny, nz;
     int rows;             // ny * nz padded rows per direction plane
     int pitch;            // floats per padded row (multiple of 32)
+    int off;              // floats from a row's start to its column 0 (8 or 32)
+    int xwrap;            // 1: the x halo columns mirror the row's own ends (periodic
+                          // x); 0: a slab, whose halos come from its neighbours
     long long plane;      // rows * pitch floats per direction
     int wall_y, wall_z;   // 1: bounce-back walls on both faces of that axis
     float omega;          // 1 / tau
@@ -57,9 +62,11 @@ struct Launch {
 };
 
 // ------------------------------------------------------- host helpers ----
-// Floats per padded row for a row of nx cells: column 0 at float VANS_OFF,
+// Floats from a row's start to its column 0 for lattice q (VDom::off).
+inline int col0_for(int q) { return q == 19 ? 32 : 8; }
+// Floats per padded row for a row of nx cells: column 0 at col0_for(q),
 // columns -1 and nx as halo copies, rounded up to whole 128-byte lines.
-int pitch_for(int nx);
+int pitch_for(int q, int nx);
 // The kernel descriptor of one domain from validated parameters: sizes, row
 // layout, relaxation and drag constants, walls.  Buffers (eps, f, status) are
 // left null for the caller to set.

@@ -93,7 +93,7 @@ __device__ __forceinline__ void issue_tile_ring(const VDom &d, const float *__re
 // comes in one or two aligned V-wide shared loads (8 or 16 bytes) and each
 // output row leaves in one V-wide global store.  Segment position p holds
 // column xs - kLead + p.
-template <int Q, int NT, int V, bool EDGE, bool PL, bool RAG, class Rel>
+template <int Q, int NT, int V, bool EDGE, bool PL, bool RAG, bool WRAP, class Rel>
 __device__ __forceinline__ void ring_tile_vec(const VDom &d, const float *__restrict__ sb,
                                               const float *const ey_slot[3], const Nb3 &Y,
                                               const Nb3 &Z, float *__restrict__ fout, int y, int z,
@@ -143,7 +143,7 @@ __device__ __forceinline__ void ring_tile_vec(const VDom &d, const float *__rest
         } else if (s < 0) {
             float A[V];
             vload(row, x0l + kLead - V, A);
-            h[i][0] = A[V - 1];
+            h[i][0] = (WRAP && x0l == 0) ? row[kLead + d.nx - 1] : A[V - 1];
 #pragma unroll
             for (int c = 1; c < V; ++c) h[i][c] = B[c - 1];
         } else {
@@ -151,7 +151,7 @@ __device__ __forceinline__ void ring_tile_vec(const VDom &d, const float *__rest
             vload(row, x0l + kLead + V, C);
 #pragma unroll
             for (int c = 0; c < V - 1; ++c) h[i][c] = B[c + 1];
-            h[i][V - 1] = C[0];
+            h[i][V - 1] = (WRAP && x0l + V == d.nx) ? row[kLead] : C[0];
         }
     }
     // eps rows (y + dy, z + dz) at columns x0l-1 .. x0l+V; a D3Q19 corner row
@@ -171,8 +171,8 @@ __device__ __forceinline__ void ring_tile_vec(const VDom &d, const float *__rest
                 float A[V], C[V];
                 vload(row, x0l + kLead - V, A);
                 vload(row, x0l + kLead + V, C);
-                E[r][q][0] = A[V - 1];
-                E[r][q][V + 1] = C[0];
+                E[r][q][0] = (WRAP && x0l == 0) ? row[kLead + d.nx - 1] : A[V - 1];
+                E[r][q][V + 1] = (WRAP && x0l + V == d.nx) ? row[kLead] : C[0];
             } else {
                 E[r][q][0] = E[r][q][V + 1] = 0.f;    // never read
             }
@@ -237,7 +237,8 @@ __device__ __forceinline__ void ring_tile_vec(const VDom &d, const float *__rest
 // code (it would raise their register count).  RAG (the batched instances,
 // whose domains end in ragged tiles): warps past the row's last column skip the
 // tile; the single-domain instances measured slower with the test in place.
-template <int Q, int NT, int CPT, bool VEC, bool EDGE, bool PL, bool RAG, class Rel>
+template <int Q, int NT, int CPT, bool VEC, bool EDGE, bool PL, bool RAG, class Rel,
+          bool WRAP = false>
 __device__ __forceinline__ void ring_tile(const VDom &d, const float *__restrict__ sb,
                                           const float *const ey_slot[3], const Nb3 &Y, const Nb3 &Z,
                                           float *__restrict__ fout, int y, int z, int xs, int tid,
@@ -245,7 +246,8 @@ __device__ __forceinline__ void ring_tile(const VDom &d, const float *__restrict
     using L = Lat<Q>;
     constexpr int SEG = NT * CPT + 2 * kLead;
     if constexpr (VEC) {
-        ring_tile_vec<Q, NT, CPT, EDGE, PL, RAG>(d, sb, ey_slot, Y, Z, fout, y, z, xs, tid, release);
+        ring_tile_vec<Q, NT, CPT, EDGE, PL, RAG, WRAP>(d, sb, ey_slot, Y, Z, fout, y, z, xs, tid,
+                                                        release);
     } else {
         // plates on nodes (PL instances only): a plate row is written by its
         // fluid neighbour row
@@ -577,7 +579,7 @@ struct IlvBatchCursor {        // a batch: tile table {dom, row, x0}, descriptor
     __device__ void next() { t += G; }
 };
 
-template <int Q, int NT, int CPT, bool VEC, bool PL, bool RAG, class Cur>
+template <int Q, int NT, int CPT, bool VEC, bool PL, bool RAG, class Cur, bool WRAP = false>
 __device__ __forceinline__ void ilv_run(Cur cur, const int *status, int ntiles, int stages,
                                         unsigned char *smem) {
     constexpr int TW = NT * CPT;
@@ -614,8 +616,8 @@ __device__ __forceinline__ void ilv_run(Cur cur, const int *status, int ntiles, 
                 if (!ok) break;
                 fence_proxy_async_smem();
             }
-            issue_tile<Q, TW>(cur.dom(), cur.fin(), cur.row(), cur.xs(TW), buf + s * (NS * SEG),
-                              &full[s]);
+            issue_tile<Q, TW, WRAP>(cur.dom(), cur.fin(), cur.row(), cur.xs(TW),
+                                    buf + s * (NS * SEG), &full[s]);
             issued = k + 1;
             cur.next();
         }
@@ -650,22 +652,22 @@ __device__ __forceinline__ void ilv_run(Cur cur, const int *status, int ntiles, 
         const int xs = cur.xs(TW);
         if (Q == 19 || Y.wall[0] || Y.wall[2] || Z.wall[0] || Z.wall[2] ||
             (PL && (y <= 1 || y >= d.ny - 2)))
-            ring_tile<Q, NT, CPT, VEC, true, PL, RAG>(d, sb, ey_slot, Y, Z, cur.fout(), y, z, xs,
-                                                      tid, release);
+            ring_tile<Q, NT, CPT, VEC, true, PL, RAG, decltype(release) &, WRAP>(
+                d, sb, ey_slot, Y, Z, cur.fout(), y, z, xs, tid, release);
         else
-            ring_tile<Q, NT, CPT, VEC, false, PL, RAG>(d, sb, ey_slot, Y, Z, cur.fout(), y, z, xs,
-                                                       tid, release);
+            ring_tile<Q, NT, CPT, VEC, false, PL, RAG, decltype(release) &, WRAP>(
+                d, sb, ey_slot, Y, Z, cur.fout(), y, z, xs, tid, release);
         cur.next();
         if (++s == stages) { s = 0; par ^= 1u; }
     }
 }
 
-template <int Q, int NT, int CPT, bool VEC, bool PL = false>
+template <int Q, int NT, int CPT, bool VEC, bool PL = false, bool WRAP = false>
 __global__ void __launch_bounds__(NT + 32) k_step_tma_ilv(const VDom d, const float *__restrict__ fin,
                                                            float *__restrict__ fout, int ntx,
                                                            int ntiles, int stages) {
     extern __shared__ __align__(128) unsigned char smem[];
-    ilv_run<Q, NT, CPT, VEC, PL, false>(
+    ilv_run<Q, NT, CPT, VEC, PL, false, IlvCursor, WRAP>(
         IlvCursor(d, fin, fout, (int)blockIdx.x, (int)gridDim.x, ntx), d.status, ntiles, stages, smem);
 }
 
@@ -710,7 +712,12 @@ static cudaError_t launch_ilv_t(const VDom &d, const float *fin, float *fout, in
     const size_t smem = kBarBytes + (size_t)stages * NS * (TW + 2 * kLead) * sizeof(float);
     if (stages < 2 || stages > kBarBytes / 16 || smem > 227 * 1024) return cudaErrorInvalidValue;
     const size_t smem_req = cap_smem(smem, ctas);
-    auto kern = k_step_tma_ilv<Q, NT, CPT, VEC, PL>;
+    // D3Q19 rows that are one tile, nx a multiple of 8, x periodic within the
+    // domain (not a slab): cells-only staging
+    constexpr bool kWrapOk = Q == 19 && VEC && !PL;
+    const bool wrap = kWrapOk && d.nx <= TW && (d.nx & 7) == 0 && d.off == 32 && d.xwrap;
+    auto kern = wrap ? k_step_tma_ilv<Q, NT, CPT, VEC, PL, kWrapOk>
+                     : k_step_tma_ilv<Q, NT, CPT, VEC, PL, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_req);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, occ = 0;

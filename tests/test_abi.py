@@ -55,7 +55,7 @@ def test_size_queries(lib):
     assert sf == 9 * 4096 * pitch
     assert wb == (2 * sf + 4096 * pitch + 64) * 4
     sf3, _ = _sizes(lib, q=19, nx=256, ny=256, nz=256, tau=0.6, wall_mask=6)
-    assert sf3 == 19 * 256 * 256 * 288
+    assert sf3 == 19 * 256 * 256 * 320  # D3Q19: column 0 on a 128-byte line, 32 + 256 + 1 -> 320
     # ragged nx: rows still start on 128-byte boundaries
     sfr, _ = _sizes(lib, q=9, nx=37, ny=5, tau=0.7)
     assert sfr % 64 == 0 and sfr >= 9 * 5 * (4 + 37 + 2)

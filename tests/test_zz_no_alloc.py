@@ -98,7 +98,7 @@ def test_static_step_refuses_domains_beyond_its_scratch_and_overlapping_buffers(
     a, b, e = 1 << 32, 1 << 40, 1 << 36          # far apart, never touched
     big = Params(q=9, nx=2048, ny=2048, wall_mask=2, tau=0.7)   # 2048 rows x 2080 floats > 4 Mi
     assert lib.vans_step_static(ctypes.byref(big.c()), e, a, b, None) == -1
-    cube = Params(q=19, nx=129, ny=129, nz=129, wall_mask=6, tau=0.7)   # pitch 288: 4.8 Mi floats
+    cube = Params(q=19, nx=129, ny=129, nz=129, wall_mask=6, tau=0.7)   # pitch 320: 5.3 Mi floats
     assert lib.vans_step_static(ctypes.byref(cube.c()), e, a, b, None) == -1
     small = Params(q=9, nx=100, ny=50, wall_mask=2, tau=0.7)
     n = lib.vans_state_floats(ctypes.byref(small.c()))
