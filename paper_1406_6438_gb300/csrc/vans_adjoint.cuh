@@ -33,6 +33,23 @@ __device__ __forceinline__ void acc2_reg(float &s, float &c, float x) {
     s = t;
 }
 
+// Add a term formed in type T: an FP64 term goes in as its FP32 leading part
+// plus the FP32 rounding of the remainder, so the accumulation keeps about 48
+// of its bits instead of 24 (the terms are large sensitivities whose sum over
+// the steps cancels to the small eps gradient).
+__device__ __forceinline__ void acc2_term(float *s, float *c, float x) { acc2(s, c, x); }
+__device__ __forceinline__ void acc2_term(float *s, float *c, double x) {
+    const float hi = (float)x;
+    acc2(s, c, hi);
+    *c += (float)(x - (double)hi);
+}
+__device__ __forceinline__ void acc2_reg_term(float &s, float &c, float x) { acc2_reg(s, c, x); }
+__device__ __forceinline__ void acc2_reg_term(float &s, float &c, double x) {
+    const float hi = (float)x;
+    acc2_reg(s, c, hi);
+    c += (float)(x - (double)hi);
+}
+
 // Square root and reciprocal of the reverse arithmetic: FP64 correctly
 // rounded; FP32 the hardware estimates refined by one Newton step (rcp_nr,
 // sqrt_nr: within about an ulp, without the division's slow-path branch).

@@ -93,9 +93,9 @@ __device__ __forceinline__ void adjoint_tile(const VDom &d, const float *__restr
                     ebar += (T)wall_gain<Q>(d, L::opp(i), 1.f) * (T)mu[cc][i];
         }
         const long long m = ((long long)z * d.ny + y) * d.nx + x;
-        acc2_reg(gs[cc][0], gc[cc][0], (float)ebar);
+        acc2_reg_term(gs[cc][0], gc[cc][0], ebar);
 #pragma unroll
-        for (int c = 0; c < D; ++c) acc2_reg(gs[cc][1 + c], gc[cc][1 + c], (float)gbar[c]);
+        for (int c = 0; c < D; ++c) acc2_reg_term(gs[cc][1 + c], gc[cc][1 + c], gbar[c]);
 #pragma unroll
         for (int c = 0; c <= D; ++c) {
             grad[c * d.cells + m] = gs[cc][c];

@@ -313,9 +313,11 @@ __global__ void k_flux_seed(const VDom d, const float *__restrict__ st, int x_ou
             lam[pull_index<Q>(d, i, x_out, y, z, Y, Z)] = (float)l;
         }
         const long long n = (long long)r * d.nx + x_out;
-        grad[n] = (float)ebar;       // sums; the compensations were zeroed with them
+        const long long nc = (1 + D) * d.cells;   // sums and compensations were zeroed
+        acc2_term(&grad[n], &grad[nc + n], ebar);
 #pragma unroll
-        for (int c = 0; c < D; ++c) grad[(1 + c) * d.cells + n] = (float)gbar[c];
+        for (int c = 0; c < D; ++c)
+            acc2_term(&grad[(1 + c) * d.cells + n], &grad[nc + (1 + c) * d.cells + n], gbar[c]);
     }
 }
 
@@ -406,10 +408,10 @@ __device__ __forceinline__ void adj_row(const VDom &d, const float *__restrict__
         if (x0 + k < d.nx) {
             const long long n = ((long long)z * d.ny + y) * d.nx + x0 + k;
             const long long nc = (1 + D) * d.cells;   // compensation words follow the sums
-            acc2(&grad[n], &grad[nc + n], (float)ebar);
+            acc2_term(&grad[n], &grad[nc + n], ebar);
 #pragma unroll
             for (int c = 0; c < D; ++c)
-                acc2(&grad[(1 + c) * d.cells + n], &grad[nc + (1 + c) * d.cells + n], (float)gbar[c]);
+                acc2_term(&grad[(1 + c) * d.cells + n], &grad[nc + (1 + c) * d.cells + n], gbar[c]);
         }
     }
 #pragma unroll
