@@ -58,13 +58,21 @@ def test_slabs_match_the_oracle_and_the_whole_domain(q, shape, wm, cuts, kw):
     sl.close()
 
 
-def test_slabs_in_a_pipelined_launch():
-    """The interleaved bulk-copy step (kind 7) on slabs of the periodic noise
-    workload, against the oracle."""
+@pytest.mark.parametrize("case", ["d2q9", "d3q19 rows of one tile"])
+def test_slabs_in_a_pipelined_launch(case):
+    """The interleaved bulk-copy step (kind 7) on slabs, against the oracle.
+    D3Q19 slabs of 64 columns are rows of one tile, which a periodic domain
+    stages cells only, taking the x wrap from the row's other end; a slab's
+    halo columns are its neighbours', so it must stage them."""
     torch = torch_cuda()
     from paper_1406_6438_gb300.slabs import Slabs
-    p, eps, _ = W.periodic_2d_shape(600, 64, nsteps=0)
-    sl = Slabs(p, eps, nslabs=2, launch=Launch(4, 4, 3, 7, 2))
+    if case == "d2q9":
+        p, eps, _ = W.periodic_2d_shape(600, 64, nsteps=0)
+        L = Launch(4, 4, 3, 7, 2)
+    else:
+        p, eps, _ = W.duct_3d(nx=128, ny=12, nz=10, nsteps=0)
+        L = Launch(2, 4, 2, 7)
+    sl = Slabs(p, eps, nslabs=2, launch=L)
     sl.step(15)
     f = sl.populations()
     torch.cuda.synchronize()
