@@ -57,6 +57,7 @@ TRAFFIC = {
 _PIPELINE_SOURCES = ("vans_step_tma.cu", "vans_pipeline.cuh", "vans_device.cuh", "vans_tma.cuh")
 KERNEL_SOURCES = {0: ("vans_step.cu", "vans_device.cuh")}
 KERNEL_SOURCES.update({k: _PIPELINE_SOURCES for k in (2, 4, 5, 6, 7)})
+KERNEL_SOURCES[8] = ("vans_cluster.cu", "vans_device.cuh")
 
 
 def kernel_hash(kind: int = 2) -> str:
@@ -72,7 +73,8 @@ KERNEL_NAMES = {0: "k_step<9,cpt>", 2: "k_step_tma_ring<9,32*warps,cpt>",
                 4: "k_step_tma_ring<9,32*warps,cpt,warp-specialised>",
                 5: "k_step_tma_ring<9,32*warps,4,contiguous,warp-specialised>",
                 6: "k_step_tma_ilv<9,32*warps,cpt,strided>",
-                7: "k_step_tma_ilv<9,32*warps,4,contiguous>"}
+                7: "k_step_tma_ilv<9,32*warps,4,contiguous>",
+                8: "k_step_cluster<9,32*warps>"}
 
 
 def peaks():

@@ -108,6 +108,14 @@ typedef struct {
  *         staged per tile, producer warp as in kinds 4, 5; 6 strided cells
  *         (D2Q9 cpt 2, D3Q19 cpt 1; warps 4 or 8), 7 consecutive cells as in
  *         kind 5.
+ * kind 8: every step of a vans_step call in ONE launch of one thread-block
+ *         cluster (up to `rows` CTAs, 2..16; `warps` 8 or 16 per CTA; cpt 1)
+ *         that keeps the whole state in its distributed shared memory for the
+ *         run, one cluster barrier per step: for domains of a few hundred KB,
+ *         whose single-step launches cost more than their work.  Accepted
+ *         only if the cluster holds the domain (D2Q9: at most 2 cells per
+ *         thread, D3Q19: 1; two copies of each CTA's rows within 227 KB) and
+ *         not for plates on nodes: VANS_ERR_UNSUPPORTED otherwise.
  * Kinds 1 and 3 are not built (VANS_ERR_ARG).
  *         The batched path takes kinds 0, 2, 4 and 5 (one CTA per strip of
  *         up to 32 rows of one domain) and 6, 7 (one table of every domain's
@@ -119,7 +127,7 @@ typedef struct {
     int kind;
     int ctas;   /* kinds 2-7: at most this many CTAs per SM (1..4; the
                    dynamic shared memory request is raised until no more
-                   fit), 0 = as many as fit; kind 0: must be 0 */
+                   fit), 0 = as many as fit; kinds 0 and 8: must be 0 */
 } vans_launch;
 
 /* ---------------------------------------------------------------- sizes -- */

@@ -95,9 +95,11 @@ class Launch:
     row strips with a porosity ring (32*warps threads, cpt cells per thread per
     tile, rows = pipeline stages); kinds 4, 5: kind 2 with a producer warp and
     per-warp stage release (5: consecutive cells per thread); kinds 6, 7:
-    persistent CTAs over interleaved row tiles.  Kinds 1 and 3 are not built.
-    ctas: at most that many CTAs per SM for the pipelined kinds (0: as many as
-    fit)."""
+    persistent CTAs over interleaved row tiles; kind 8: every step of a call
+    in one launch of one thread-block cluster holding the state in shared
+    memory (rows = the largest cluster, warps 8 or 16, cpt 1).  Kinds 1 and 3
+    are not built.  ctas: at most that many CTAs per SM for the pipelined
+    kinds (0: as many as fit)."""
     cpt: int
     warps: int
     rows: int
