@@ -114,8 +114,8 @@ typedef struct {
  *         run, one cluster barrier per step: for domains of a few hundred KB,
  *         whose single-step launches cost more than their work.  Accepted
  *         only if the cluster holds the domain (D2Q9: at most 2 cells per
- *         thread, D3Q19: 1; two copies of each CTA's rows within 227 KB) and
- *         not for plates on nodes: VANS_ERR_UNSUPPORTED otherwise.
+ *         thread, D3Q19: 1; two copies of each CTA's rows within 227 KB):
+ *         VANS_ERR_UNSUPPORTED otherwise.  Plates on nodes included.
  * Kinds 1 and 3 are not built (VANS_ERR_ARG).
  *         The batched path takes kinds 0, 2, 4 and 5 (one CTA per strip of
  *         up to 32 rows of one domain) and 6, 7 (one table of every domain's

@@ -52,6 +52,10 @@ __device__ __forceinline__ float ld_cluster(uint32_t addr) {
     return v;
 }
 
+__device__ __forceinline__ void st_cluster(uint32_t addr, float v) {
+    asm volatile("st.shared::cluster.f32 [%0], %1;" :: "r"(addr), "f"(v) : "memory");
+}
+
 }  // namespace
 
 // Every thread keeps at most CellsMax<Q>::N cells of its CTA's band for the
@@ -61,7 +65,12 @@ __device__ __forceinline__ float ld_cluster(uint32_t addr) {
 // the CTA that owns the row) of each of the Q entries its pull reads, and its
 // own and its neighbours' porosities.  A step is then Q loads, the collision
 // and Q stores per cell.
-template <int Q, int NT>
+// PL (plates on nodes, wall_kind 1): rows 0 and ny-1 are plate nodes and are
+// not stepped; the fluid row next to a plate writes the plate node's inward
+// populations (f^eq of the plate plus this cell's non-equilibrium part,
+// relaxed), as the other step kernels do, into the plate row's entries, which
+// may lie in the neighbouring CTA's band (a store through the cluster window).
+template <int Q, int NT, bool PL>
 __global__ void __launch_bounds__(NT) k_step_cluster(const VDom d, const float *fin, float *fout,
                                                      int nsteps, int band) {
     using L = Lat<Q>;
@@ -91,6 +100,11 @@ __global__ void __launch_bounds__(NT) k_step_cluster(const VDom d, const float *
     int dst[kCellsMax], xs[kCellsMax];
     bool top[kCellsMax], live[kCellsMax];
     Nb3 Zs[kCellsMax];
+    // plates on nodes: sides (bit 0 the plate below, bit 1 the plate above:
+    // both for the one fluid row between plates 2 rows apart), and each plate
+    // row's entry of this column (copy 0, plane 0, cluster window)
+    int pside[kCellsMax];
+    uint32_t pdst[kCellsMax][2];
 #pragma unroll
     for (int k = 0; k < kCellsMax; ++k) {
         const int t = threadIdx.x + k * NT;
@@ -98,6 +112,21 @@ __global__ void __launch_bounds__(NT) k_step_cluster(const VDom d, const float *
         const int tt = live[k] ? t : 0;
         const int rl = tt / nx, x = tt - rl * nx;
         const int r = r0 + rl, y = r % d.ny, z = r / d.ny;
+        pside[k] = 0;
+        pdst[k][0] = pdst[k][1] = 0;
+        if (PL) {
+            if (y == 0 || y == d.ny - 1) live[k] = false;          // plate node: not stepped
+            if (live[k]) {
+                pside[k] = (y == 1 ? 1 : 0) | (y == d.ny - 2 ? 2 : 0);
+#pragma unroll
+                for (int side = 0; side < 2; ++side) {
+                    if (!(pside[k] & (1 << side))) continue;
+                    const int rp = side == 0 ? r - 1 : r + 1, owner = rp / band;
+                    pdst[k][side] =
+                        cluster_addr(sm + (long long)(rp - owner * band) * sp + 1 + x, owner);
+                }
+            }
+        }
         const Nb3 Y = nb3<true>(y, d.ny, d.wall_y);
         Nb3 Z;
         if (Q == 19) {
@@ -148,13 +177,40 @@ __global__ void __launch_bounds__(NT) k_step_cluster(const VDom d, const float *
             for (int i = 0; i < Q; ++i) h[i] = ld_cluster(src[k][i] + cur);
             apply_moving_wall<Q>(d, top[k], Zs[k], e0[k], h);
             float o[Q];
-            collide<Q>(d, h, e0[k], et[k], o);
+            Macro<Q> M;
+            collide<Q>(d, h, e0[k], et[k], o, (PL && pside[k]) ? &M : nullptr);
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 float *row = nxt + (long long)i * band * sp + dst[k];   // this cell's column
                 row[0] = o[i];
                 if (xs[k] == 0 && L::ex(i) < 0) row[nx] = o[i];         // halo copies of the wrap
                 if (xs[k] == nx - 1 && L::ex(i) > 0) row[-nx] = o[i];
+            }
+            if (PL && pside[k]) {
+                // the plate node's populations toward this row: e_y > 0 from
+                // the plate below, e_y < 0 from the plate above, each stored
+                // against the porosity of the row cell it streams to
+                constexpr int jym = dir_index<Q>(0, -1, 0), jyp = dir_index<Q>(0, 1, 0);
+                constexpr int jxp = dir_index<Q>(1, 0, 0), jxm = dir_index<Q>(-1, 0, 0);
+                constexpr int jzp = dir_index<Q>(0, 0, 1), jzm = dir_index<Q>(0, 0, -1);
+                const float om1 = 1.f - d.omega, zero[3] = {0.f, 0.f, 0.f};
+                const uint32_t next = (uint32_t)((b ^ 1) * copy * sizeof(float));
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    const int ey = L::ey(i);
+                    if (ey == 0 || !(pside[k] & (ey > 0 ? 1 : 2))) continue;
+                    const bool lo = ey > 0;
+                    const int ex = L::ex(i), ez = L::ez(i);
+                    const float enb = ex > 0 ? et[k][jxp] : ex < 0 ? et[k][jxm]
+                                    : ez > 0 ? et[k][jzp] : ez < 0 ? et[k][jzm] : e0[k];
+                    const float v = plate_value<Q>(d, i, h[i], M, lo ? et[k][jym] : et[k][jyp], enb,
+                                                   lo ? zero : d.uw, om1);
+                    const uint32_t a = pdst[k][lo ? 0 : 1] + next +
+                                       (uint32_t)((long long)i * band * sp * sizeof(float));
+                    st_cluster(a, v);
+                    if (xs[k] == 0 && ex < 0) st_cluster(a + (uint32_t)(nx * sizeof(float)), v);
+                    if (xs[k] == nx - 1 && ex > 0) st_cluster(a - (uint32_t)(nx * sizeof(float)), v);
+                }
             }
         }
         cl.sync();
@@ -184,7 +240,7 @@ size_t cluster_smem_bytes(int q, const VDom &d, int cmax) {
 }
 
 bool cluster_fits(int q, const VDom &d, int cmax, int warps) {
-    if (d.nee || cmax < 1 || cmax > kClusterMax) return false;
+    if (cmax < 1 || cmax > kClusterMax) return false;
     int band = 0, ctas = 0;
     cluster_shape(d, cmax, band, ctas);
     const int cells_max = (q == 9) ? CellsMax<9>::N : CellsMax<19>::N;
@@ -198,7 +254,7 @@ static cudaError_t launch_cluster_t(const VDom &d, const float *fin, float *fout
     int band = 0, ctas = 0;
     cluster_shape(d, cmax, band, ctas);
     const size_t smem = cluster_smem_bytes(Q, d, cmax);
-    auto kern = k_step_cluster<Q, NT>;
+    auto kern = d.nee ? k_step_cluster<Q, NT, true> : k_step_cluster<Q, NT, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (ctas > 8) {

@@ -902,7 +902,7 @@ static bool plate_shape(int q, const Launch &L) {
            ((L.kind == 5 || L.kind == 7) && nt == 128 && L.cpt == 2);
 }
 
-bool launch_has_plates(int q, Launch L) { return L.kind == 0 || plate_shape(q, L); }
+bool launch_has_plates(int q, Launch L) { return L.kind == 0 || L.kind == 8 || plate_shape(q, L); }
 
 static cudaError_t launch_plates(int q, const VDom &d, const float *fin, float *fout, Launch L,
                                  cudaStream_t stream) {

@@ -31,6 +31,12 @@ CASES = [
     (9, (1, 17, 45), 2, dict(u_wall=(0.02, 0.005, 0.0))),
     (19, (7, 9, 21), 6, {}),
     (19, (5, 6, 12), 2, dict(u_wall=(0.01, 0.0, 0.004))),
+    # plates on nodes (the paper's boundary scheme): rows 0 and ny-1 are not
+    # stepped, the rows next to them write the plates' inward populations,
+    # across the bands of two CTAs where a band ends next to a plate
+    (9, (1, 19, 40), 2, dict(wall_kind=1, u_wall=(0.015, 0.0, 0.0))),
+    (9, (1, 3, 24), 2, dict(wall_kind=1, u_wall=(0.01, 0.0, 0.0))),
+    (19, (4, 9, 16), 2, dict(wall_kind=1, u_wall=(0.01, 0.0, 0.005))),
 ]
 
 
@@ -61,8 +67,8 @@ def test_channel_128x64_5000_steps_in_one_launch():
 
 def test_cluster_calls_compose_and_refusals():
     """Calls of several lengths continue each other (the state and its parity
-    are where single steps leave them); plates on nodes and domains too large
-    for one cluster are refused."""
+    are where single steps leave them); domains too large for one cluster are
+    refused."""
     torch = torch_cuda()
     p, eps, _ = W.periodic_2d_shape(90, 40, nsteps=0)
     a = solver(p, eps, launch=Launch(1, 16, 16, 8))
@@ -78,8 +84,18 @@ def test_cluster_calls_compose_and_refusals():
     with pytest.raises(VansError) as ex:
         s.launch = Launch(1, 16, 16, 8)
     assert ex.value.status == -5
-    pl = W.params(q=9, nx=40, ny=12, wall_mask=2, tau=0.8, wall_kind=1)
-    s2 = solver(pl, np.full((1, 12, 40), 0.5, dtype=np.float32))
-    with pytest.raises(VansError) as ex:
-        s2.launch = Launch(1, 16, 16, 8)
-    assert ex.value.status == -5
+
+
+@pytest.mark.parametrize("Re,Da", [(1.0, 1e-3), (50.0, 1e-2)])
+def test_porous_couette_of_the_paper_in_one_cluster_launch(Re, Da):
+    """The paper's porous Couette case with its own boundary scheme (plates on
+    nodes, 81 rows), all steps in one cluster launch, against the oracle and
+    against the register-load kernel's single steps."""
+    p, eps = W.couette_80(Re=Re, Da=Da, wall_kind=1)
+    n = 400
+    rho_o, u_o, f_o = oracle_run(p, eps, n)
+    _, _, f_ref = gpu_run(p, eps, n, launch=Launch(1, 4, 1))
+    rho, u, f = gpu_run(p, eps, n, launch=Launch(1, 16, 16, 8))
+    assert rel_u(u, u_o) <= 1e-5, rel_u(u, u_o)
+    assert np.abs(f - f_o).max() <= 2e-7
+    assert np.abs(f - f_ref).max() <= 6e-8
