@@ -22,6 +22,18 @@
 
 namespace vans {
 
+// ------------------------------------------- programmatic dependent launch ----
+// A step kernel launched with the programmatic-serialization attribute may
+// start while the previous kernel of its stream is still finishing: each of its
+// CTAs first lets the NEXT kernel launch (pdl_trigger: that kernel is scheduled
+// once every CTA of this one has triggered or exited, so its CTAs only take SM
+// slots this grid no longer needs), then waits until the previous kernel has
+// completed and its writes are visible (pdl_wait), before touching memory.  A
+// launch without the attribute, or one after a non-kernel operation, waits as
+// usual and both instructions return at once.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // ------------------------------------------------------------ lattices ----
 // D2Q9 and D3Q19 velocity sets and weights (Qian, d'Humieres & Lallemand 1992,
 // the lattice family of Eq. d2q9eq), in the direction order of vans.h.

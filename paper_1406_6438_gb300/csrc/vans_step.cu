@@ -172,6 +172,8 @@ __device__ __forceinline__ void step_row(const VDom &d, const float *__restrict_
 template <int Q, int CPT, bool EMIT = false, bool PL = false>
 __global__ void __launch_bounds__(256) k_step(const VDom d, const float *__restrict__ fin,
                                               float *__restrict__ fout, int nxb, Monitor mon = {}) {
+    pdl_trigger();
+    pdl_wait();
     const int lane = threadIdx.x & 31;
     const int wx = threadIdx.x >> 5;
     const int bx = blockIdx.x % nxb;
@@ -225,11 +227,19 @@ static cudaError_t launch_step_t(const VDom &d, const float *fin, float *fout, L
     const int nrb = (d.rows + L.rows - 1) / L.rows;
     const long long nblocks = (long long)nxb * nrb;
     if (nblocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    dim3 block(32 * L.warps, L.rows);
-    if (d.nee)
-        k_step<Q, CPT, false, true><<<(unsigned)nblocks, block, 0, stream>>>(d, fin, fout, nxb);
-    else
-        k_step<Q, CPT><<<(unsigned)nblocks, block, 0, stream>>>(d, fin, fout, nxb);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)nblocks, 1, 1);
+    cfg.blockDim = dim3(32 * L.warps, L.rows, 1);
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;   // see pdl_trigger
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const Monitor none{};
+    cudaError_t e = d.nee ? cudaLaunchKernelEx(&cfg, k_step<Q, CPT, false, true>, d, fin, fout, nxb, none)
+                          : cudaLaunchKernelEx(&cfg, k_step<Q, CPT, false, false>, d, fin, fout, nxb, none);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
