@@ -650,7 +650,10 @@ __device__ __forceinline__ void ilv_run(Cur cur, const int *status, int ntiles, 
             if (lane == 0) mbar_arrive(emp);
         };
         const int xs = cur.xs(TW);
-        if (Q == 19 || Y.wall[0] || Y.wall[2] || Z.wall[0] || Z.wall[2] ||
+        // (D3Q19 too: here a second copy of the tile code, for the rows away
+        // from walls, is faster -- 256^3 duct 0.937 -> 0.969 of the copy
+        // bandwidth -- unlike in the strip kernels)
+        if (Y.wall[0] || Y.wall[2] || Z.wall[0] || Z.wall[2] ||
             (PL && (y <= 1 || y >= d.ny - 2)))
             ring_tile<Q, NT, CPT, VEC, true, PL, RAG, decltype(release) &, WRAP>(
                 d, sb, ey_slot, Y, Z, cur.fout(), y, z, xs, tid, release);

@@ -58,6 +58,10 @@ STEP_CASES = [
     (19, (2, 4, 256), 2, [Launch(2, 4, 2, 7), Launch(2, 2, 3, 7), Launch(1, 8, 2, 6),
                           Launch(1, 4, 3, 6)]),
     (19, (2, 3, 8), 6, [Launch(2, 4, 2, 7), Launch(1, 4, 2, 6)]),
+    # rows shorter than the tile staged cells-only: lanes past nx idle, the x
+    # wrap read from the other end of the staged cells
+    (19, (3, 7, 96), 6, [Launch(2, 4, 2, 7), Launch(2, 4, 3, 7, 2), Launch(2, 2, 2, 7)]),
+    (19, (5, 3, 40), 2, [Launch(2, 2, 3, 7), Launch(2, 4, 2, 7)]),
 ]
 
 
