@@ -227,20 +227,10 @@ static cudaError_t launch_step_t(const VDom &d, const float *fin, float *fout, L
     const int nrb = (d.rows + L.rows - 1) / L.rows;
     const long long nblocks = (long long)nxb * nrb;
     if (nblocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)nblocks, 1, 1);
-    cfg.blockDim = dim3(32 * L.warps, L.rows, 1);
-    cfg.stream = stream;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;   // see pdl_trigger
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    const dim3 grid((unsigned)nblocks), block(32 * L.warps, L.rows);
     const Monitor none{};
-    cudaError_t e = d.nee ? cudaLaunchKernelEx(&cfg, k_step<Q, CPT, false, true>, d, fin, fout, nxb, none)
-                          : cudaLaunchKernelEx(&cfg, k_step<Q, CPT, false, false>, d, fin, fout, nxb, none);
-    if (e != cudaSuccess) return e;
-    return cudaGetLastError();
+    return d.nee ? launch_pdl(k_step<Q, CPT, false, true>, grid, block, 0, stream, d, fin, fout, nxb, none)
+                 : launch_pdl(k_step<Q, CPT, false, false>, grid, block, 0, stream, d, fin, fout, nxb, none);
 }
 
 cudaError_t launch_step(int q, const VDom &d, const float *fin, float *fout, Launch L,
