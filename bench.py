@@ -275,7 +275,8 @@ def bench_d3q19(torch, V, W, args=None):
     c0 = s.launch_count
     t = time_region(torch, s.stream, lambda: s.step(n))
     cells = p["nx"] * p["ny"] * p["nz"]
-    out = {"workload": "D3Q19 256^3, walls y/z, eps noise [0.35,0.95], tau 0.6, Forchheimer",
+    size = "%d^3" % p["nx"] if p["nx"] == p["ny"] == p["nz"] else "%dx%dx%d" % (p["nx"], p["ny"], p["nz"])
+    out = {"workload": "D3Q19 %s, walls y/z, eps noise [0.35,0.95], tau 0.6, Forchheimer" % size,
            "steps": n, "value": cells * n / t / 1e6, "unit": "MLUPS",
            "gb_s": BYTES_PER_CELL[19] * cells * n / t / 1e9,
            "launch": vars(L), "launches": s.launch_count - c0}

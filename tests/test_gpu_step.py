@@ -62,6 +62,12 @@ STEP_CASES = [
     # wrap read from the other end of the staged cells
     (19, (3, 7, 96), 6, [Launch(2, 4, 2, 7), Launch(2, 4, 3, 7, 2), Launch(2, 2, 2, 7)]),
     (19, (5, 3, 40), 2, [Launch(2, 2, 3, 7), Launch(2, 4, 2, 7)]),
+    # 384-cell tiles (6 compute warps): rows of 384 and 264 cells staged
+    # cells-only, 300 (not a multiple of 8) and 600 cells with their halos
+    (19, (2, 3, 384), 6, [Launch(2, 6, 2, 7), Launch(2, 6, 3, 7, 1)]),
+    (19, (3, 2, 264), 2, [Launch(2, 6, 2, 7)]),
+    (19, (2, 2, 300), 6, [Launch(2, 6, 2, 7)]),
+    (19, (2, 3, 600), 0, [Launch(2, 6, 2, 7)]),
 ]
 
 
@@ -449,7 +455,8 @@ def test_cta_cap_refusals_and_roundtrip():
     p, eps, _ = W.periodic_2d_shape(64, 16, nsteps=0)
     s = solver(p, eps)
     for L in (Launch(4, 4, 1, 0, 1), Launch(4, 4, 2, 7, 5), Launch(4, 4, 2, 7, -1),
-              Launch(2, 4, 3, 1), Launch(4, 4, 3, 3)):      # kinds 1 and 3 are not built
+              Launch(2, 4, 3, 1), Launch(4, 4, 3, 3),       # kinds 1 and 3 are not built
+              Launch(4, 6, 2, 7)):                          # 6 warps: D3Q19 only
         with pytest.raises(VansError):
             s.launch = L
     with pytest.raises(VansError):
