@@ -68,6 +68,10 @@ STEP_CASES = [
     (19, (3, 2, 264), 2, [Launch(2, 6, 2, 7)]),
     (19, (2, 2, 300), 6, [Launch(2, 6, 2, 7)]),
     (19, (2, 3, 600), 0, [Launch(2, 6, 2, 7)]),
+    # 192-cell tiles (3 compute warps)
+    (19, (3, 3, 192), 6, [Launch(2, 3, 2, 7), Launch(2, 3, 3, 7, 2)]),
+    (19, (2, 5, 136), 2, [Launch(2, 3, 2, 7)]),
+    (19, (2, 2, 250), 6, [Launch(2, 3, 2, 7)]),
 ]
 
 
