@@ -53,6 +53,14 @@ __device__ __forceinline__ void pull_cell(const VDom &d, const float *__restrict
 }
 
 __device__ __forceinline__ void cell_xyz(const VDom &d, long long n, int &x, int &y, int &z) {
+    if (d.cells <= 0xffffffffLL) {                // 32-bit divisions where they suffice
+        const unsigned m = (unsigned)n, nx = (unsigned)d.nx, ny = (unsigned)d.ny;
+        const unsigned r = m / nx;
+        x = (int)(m - r * nx);
+        y = (int)(r % ny);
+        z = (int)(r / ny);
+        return;
+    }
     x = (int)(n % d.nx);
     const long long r = n / d.nx;
     y = (int)(r % d.ny);
