@@ -107,8 +107,8 @@ typedef struct {
  *         tile order (the whole grid sweeps one band of rows), porosity rows
  *         staged per tile, producer warp as in kinds 4, 5; 6 strided cells
  *         (D2Q9 cpt 2, D3Q19 cpt 1; warps 4 or 8), 7 consecutive cells as in
- *         kind 5 (single D3Q19 domains also warps 3 or 6: 192- or 384-cell
- *         tiles).
+ *         kind 5 (single D3Q19 domains also warps 3, 5 or 6: 192-, 320- or
+ *         384-cell tiles).
  * kind 8: every step of a vans_step call in ONE launch of one thread-block
  *         cluster (up to `rows` CTAs, 2..16; `warps` 8 or 16 per CTA; cpt 1)
  *         that keeps the whole state in its distributed shared memory for the

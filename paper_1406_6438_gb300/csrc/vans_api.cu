@@ -94,7 +94,8 @@ bool launch_ok(const vans_launch *c, int q, bool batched) {
     if (c->rows < 2 || c->rows > 6) return false;
     // the instantiated pipeline shapes
     const int nt = 32 * c->warps;
-    if (c->kind == 7 && q == 19 && (nt == 96 || nt == 192))   // 192-, 384-cell D3Q19 tiles
+    if (c->kind == 7 && q == 19 && (nt == 96 || nt == 160 || nt == 192))
+        // 192-, 320-, 384-cell D3Q19 tiles
         return c->cpt == 2 && !batched;
     if (c->kind == 5 || c->kind == 7)
         return (nt == 64 || nt == 128) && c->cpt == (q == 9 ? 4 : 2) && (q == 9 || !batched);
@@ -488,7 +489,7 @@ std::vector<Launch> candidates(int q, bool batched) {
                             {1, 8, 3, 6}, {2, 4, 3, 7}, {2, 2, 3, 7}, {2, 4, 2, 7},
                             {2, 4, 2, 7, 2}, {2, 4, 2, 7, 1}, {2, 4, 3, 7, 1}, {2, 4, 3, 7, 2},
                             {2, 4, 2, 5, 2}, {2, 2, 2, 7}, {2, 2, 4, 7}, {2, 6, 2, 7},
-                            {2, 3, 2, 7}, {2, 3, 3, 7}};
+                            {2, 3, 2, 7}, {2, 3, 3, 7}, {2, 5, 2, 7}};
         c.insert(c.end(), std::begin(t), std::end(t));
     }
     // cluster-resident multi-step shapes {1, warps, largest cluster, 8}; the

@@ -72,6 +72,10 @@ STEP_CASES = [
     (19, (3, 3, 192), 6, [Launch(2, 3, 2, 7), Launch(2, 3, 3, 7, 2)]),
     (19, (2, 5, 136), 2, [Launch(2, 3, 2, 7)]),
     (19, (2, 2, 250), 6, [Launch(2, 3, 2, 7)]),
+    # 320-cell tiles (5 compute warps): rows of one tile and of two
+    (19, (2, 3, 320), 6, [Launch(2, 5, 2, 7), Launch(2, 5, 3, 7, 1)]),
+    (19, (3, 2, 512), 2, [Launch(2, 5, 2, 7)]),
+    (19, (2, 2, 296), 0, [Launch(2, 5, 2, 7)]),
 ]
 
 
