@@ -136,8 +136,9 @@ typedef struct {
 /* Floats in one state buffer for these parameters, or -1 if they are invalid. */
 long long vans_state_floats(const vans_params *p);
 
-/* Bytes of workspace vans_create needs (two state buffers, a padded copy of eps
- * and a few status words), or 0 if the parameters are invalid. */
+/* Bytes of workspace vans_create needs (two state buffers, a padded copy of eps,
+ * a few status words and the partial maxima of vans_step_monitored), or 0 if
+ * the parameters are invalid. */
 size_t vans_workspace_bytes(const vans_params *p);
 
 /* ------------------------------------------------------------ lifecycle -- */

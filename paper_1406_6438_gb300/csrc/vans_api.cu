@@ -43,6 +43,7 @@ long long eps_floats_of(int q, int nx, int ny, int nz) {
 }
 
 constexpr long long kFlagFloats = 64;   // 256 bytes of status words
+constexpr long long kMonFloats = 3 * vans::kMonSlots;   // partial maxima of vans_step_monitored
 
 int validate(const vans_params *p, bool batched) {
     if (!p) return VANS_ERR_ARG;
@@ -169,6 +170,7 @@ struct vans_s {
     Launch L{4, 4, 1, 0};
     cudaGraphExec_t gexec[kGraphSizes] = {};   // 64, 32, ..., 2 steps
     int *flag = nullptr;                        // device status words (workspace)
+    float *mon_part = nullptr;                  // monitoring partial maxima (workspace)
     int adj_fp64 = 0;                           // reverse-step arithmetic in FP64
     Launch adjL{1, 4, 4, 1};                    // reverse-step launch shape
     // single domain
@@ -512,7 +514,7 @@ long long vans_state_floats(const vans_params *p) {
 size_t vans_workspace_bytes(const vans_params *p) {
     if (validate(p, false) != VANS_OK) return 0;
     const long long f = 2 * state_floats_of(p->q, p->nx, p->ny, p->nz) +
-                        eps_floats_of(p->q, p->nx, p->ny, p->nz) + kFlagFloats;
+                        eps_floats_of(p->q, p->nx, p->ny, p->nz) + kFlagFloats + kMonFloats;
     return (size_t)f * sizeof(float);
 }
 
@@ -537,6 +539,7 @@ int vans_create(const vans_params *p, void *workspace, size_t workspace_bytes, v
     h->flag = (int *)(h->eps_pad + eps_floats_of(p->q, p->nx, p->ny, p->nz));
     h->dom.eps = h->eps_pad;
     h->dom.status = h->flag + 1;
+    h->mon_part = (float *)(h->flag + kFlagFloats);
     h->L = (p->q == 9) ? Launch{4, 4, 1, 0} : Launch{2, 4, 1, 0};
     // the pipelined reverse step, one cell per thread, 4 stages: fastest on GB300 at 512^2
     // (backward pass 17.4 us per step against 20.8 with the register-load kernel)
@@ -622,7 +625,8 @@ int vans_step_monitored(vans_t h, int nsteps, int every, float *rho_dev, float *
         return VANS_ERR_ARG;
     if (h->dom.nee || h->slab) return VANS_ERR_UNSUPPORTED;    // plates on nodes: use vans_moments
     if (!h->eps_set) return VANS_ERR_STATE;
-    if (cudaMemsetAsync(stats_dev, 0, 4 * sizeof(float), h->stream) != cudaSuccess)
+    if (cudaMemsetAsync(stats_dev, 0, 4 * sizeof(float), h->stream) != cudaSuccess ||
+        cudaMemsetAsync(h->mon_part, 0, kMonFloats * sizeof(float), h->stream) != cudaSuccess)
         return VANS_ERR_CUDA;
     int done = 0;
     while (done < nsteps) {
@@ -635,10 +639,15 @@ int vans_step_monitored(vans_t h, int nsteps, int every, float *rho_dev, float *
         }
         ++h->launches;
         if (vans::launch_step_monitor(h->q, h->dom, h->st[h->cur], h->st[h->cur ^ 1], rho_dev, u_dev,
-                                      stats_dev, h->stream) != cudaSuccess)
+                                      stats_dev, h->mon_part, h->stream) != cudaSuccess)
             return VANS_ERR_CUDA;
         h->cur ^= 1;
         ++done;
+    }
+    if (nsteps > 0) {
+        ++h->launches;
+        if (vans::launch_monitor_finalize(h->mon_part, stats_dev, h->stream) != cudaSuccess)
+            return VANS_ERR_CUDA;
     }
     return VANS_OK;
 }

@@ -77,8 +77,12 @@ void fill_dom(const vans_params *p, VDom &d);
 
 cudaError_t launch_step(int q, const VDom &d, const float *fin, float *fout, Launch L,
                         cudaStream_t stream);
+// partial maxima of the monitoring reductions: kMonSlots per statistic
+constexpr int kMonSlots = 256;
 cudaError_t launch_step_monitor(int q, const VDom &d, const float *fin, float *fout, float *rho,
-                                float *u, float *stats, cudaStream_t stream);
+                                float *u, float *stats, float *part, cudaStream_t stream);
+// stats[0..2] = maxima of the partials (after the monitoring steps of a call)
+cudaError_t launch_monitor_finalize(const float *part, float *stats, cudaStream_t stream);
 cudaError_t launch_step_tma(int q, const VDom &d, const float *fin, float *fout, Launch L,
                             cudaStream_t stream);
 // kind 8: nsteps steps in one launch of one thread-block cluster that holds the

@@ -53,7 +53,7 @@ def test_size_queries(lib):
     sf, wb = _sizes(lib, q=9, nx=4096, ny=4096, tau=0.6)
     pitch = 4128                       # 8 + round_up(4096, 128) + 1, rounded up to 32
     assert sf == 9 * 4096 * pitch
-    assert wb == (2 * sf + 4096 * pitch + 64) * 4
+    assert wb == (2 * sf + 4096 * pitch + 64 + 3 * 256) * 4   # states, eps, status, monitor partials
     sf3, _ = _sizes(lib, q=19, nx=256, ny=256, nz=256, tau=0.6, wall_mask=6)
     assert sf3 == 19 * 256 * 256 * 320  # D3Q19: column 0 on a 128-byte line, 32 + 256 + 1 -> 320
     # ragged nx: rows still start on 128-byte boundaries
