@@ -211,13 +211,17 @@ __global__ void k_rebase_eps(const VDom d, const float *__restrict__ eps_new, fl
         const float e_old = d.eps[row_offset(d, y, z) + x];
         const float e_new = eps_new[n];
         const bool top = d.moving && Y.wall[2];
+        // every entry read before any is written: interleaved, each load had to
+        // wait for the store before it (the same pointer)
+        float v[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) v[i] = st[pull_index<Q>(d, i, x, y, z, Y, Z)];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const long long k = pull_index<Q>(d, i, x, y, z, Y, Z);
-            float v = st[k] + L::w(i) * (e_old - e_new);
+            v[i] += L::w(i) * (e_old - e_new);
             if (top && L::ey(i) < 0 && !Z.wall[1 - L::ez(i)])
-                v += wall_gain<Q>(d, i, e_old) - wall_gain<Q>(d, i, e_new);
-            store_pulled<Q>(d, st, i, x, y, z, Y, Z, v);
+                v[i] += wall_gain<Q>(d, i, e_old) - wall_gain<Q>(d, i, e_new);
+            store_pulled<Q>(d, st, i, x, y, z, Y, Z, v[i]);
         }
     }
 }
@@ -229,8 +233,16 @@ __global__ void k_pad_eps(const VDom d, const float *__restrict__ eps, float *__
     const long long total = (long long)d.rows * d.pitch;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
-        const long long r = t / d.pitch;
-        const int c = (int)(t % d.pitch) - d.off;
+        long long r;
+        int c;
+        if (total <= 0xffffffffLL) {            // 32-bit division where it suffices
+            const unsigned tt = (unsigned)t, rr = tt / (unsigned)d.pitch;
+            r = rr;
+            c = (int)(tt - rr * (unsigned)d.pitch) - d.off;
+        } else {
+            r = t / d.pitch;
+            c = (int)(t % d.pitch) - d.off;
+        }
         float v = 1.0f;
         if (c >= 0 && c < d.nx) {
             v = eps[r * d.nx + c];
