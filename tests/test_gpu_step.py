@@ -322,6 +322,9 @@ MOVING = [
                                           Launch(2, 4, 2, 5)]),
     (19, (5, 7, 64), 6, (0.01, 0.0, 0.004), [Launch(2, 4, 2, 7), Launch(1, 4, 2, 6),
                                              Launch(2, 2, 2, 7)]),
+    # the 192-, 320- and 384-cell D3Q19 tiles (3, 5 and 6 warps)
+    (19, (3, 5, 192), 6, (0.01, 0.0, 0.004), [Launch(2, 3, 2, 7), Launch(2, 5, 2, 7),
+                                              Launch(2, 6, 2, 7)]),
 ]
 
 
