@@ -89,3 +89,10 @@ def test_plates_on_nodes_refusals():
     # the flux (a diagnostic) is defined: sum of eps rho u_x over the column
     J = s.flux(20)
     assert np.isfinite(float(J.item()))
+    # the 192-, 320- and 384-cell D3Q19 tiles have no plates-on-nodes instance
+    p3, eps3, _ = _case(19, (3, 10, 192), (0.01, 0.0, 0.0), seed=4)
+    s3 = solver(p3, eps3)
+    for L in (Launch(2, 3, 2, 7), Launch(2, 5, 2, 7), Launch(2, 6, 2, 7)):
+        with pytest.raises(VansError):
+            s3.launch = L
+    s3.launch = Launch(2, 4, 2, 7)
