@@ -58,20 +58,30 @@ def test_slabs_match_the_oracle_and_the_whole_domain(q, shape, wm, cuts, kw):
     sl.close()
 
 
-@pytest.mark.parametrize("case", ["d2q9", "d3q19 rows of one tile"])
+@pytest.mark.parametrize("case", ["d2q9", "d3q19 rows of one tile", "d2q9 cluster-resident",
+                                  "d3q19 cluster-resident"])
 def test_slabs_in_a_pipelined_launch(case):
-    """The interleaved bulk-copy step (kind 7) on slabs, against the oracle.
-    D3Q19 slabs of 64 columns are rows of one tile, which a periodic domain
-    stages cells only, taking the x wrap from the row's other end; a slab's
-    halo columns are its neighbours', so it must stage them."""
+    """The interleaved bulk-copy step (kind 7) and the cluster-resident step
+    (kind 8) on slabs, against the oracle.  D3Q19 slabs of 64 columns are rows
+    of one tile, which a periodic domain stages cells only, taking the x wrap
+    from the row's other end; a slab's halo columns are its neighbours', so it
+    must stage them."""
     torch = torch_cuda()
     from paper_1406_6438_gb300.slabs import Slabs
     if case == "d2q9":
         p, eps, _ = W.periodic_2d_shape(600, 64, nsteps=0)
         L = Launch(4, 4, 3, 7, 2)
-    else:
+    elif case == "d3q19 rows of one tile":
         p, eps, _ = W.duct_3d(nx=128, ny=12, nz=10, nsteps=0)
         L = Launch(2, 4, 2, 7)
+    elif case == "d2q9 cluster-resident":
+        # kind 8, one step per call: the halo columns the exchange wrote are
+        # loaded with the band
+        p, eps, _ = W.periodic_2d_shape(96, 40, nsteps=0)
+        L = Launch(1, 16, 16, 8)
+    else:
+        p, eps, _ = W.duct_3d(nx=24, ny=9, nz=7, nsteps=0)
+        L = Launch(1, 16, 16, 8)
     sl = Slabs(p, eps, nslabs=2, launch=L)
     sl.step(15)
     f = sl.populations()
